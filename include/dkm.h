@@ -1,0 +1,226 @@
+/*
+ * dkm.h -- C ABI of libdkm: GB300-native indexed k-means (Lloyd's algorithm
+ * with index-based batch pruning) for 2D / 3D float32 points.
+ *
+ * Method: Dask-means, arXiv 2412.02244.
+ *   - Eq. 1 / Section II-A: k-means minimises the sum of squared errors
+ *     (SSE); Lloyd's algorithm alternates assignment (nearest centroid) and
+ *     update (cluster mean).
+ *   - Section II-B: index-based acceleration returns exactly Lloyd's result.
+ *   - Section IV-A ("Pruning Mechanisms", Eq. for the ball-node test, the
+ *     two-nearest gap test and the kNN bounds inherited from parent nodes):
+ *     a group of spatially close points is assigned in batch after pruning
+ *     centroids with distance bounds; here the groups are Morton-ordered
+ *     tiles with axis-aligned bounding boxes and the centroid index is a
+ *     uniform grid rebuilt every iteration.
+ *   - Section V-A (memory-tunable index, Eq. for f under a memory budget):
+ *     the centroid grid's cell size grows until the index fits
+ *     dkm_options.mem_budget_bytes.
+ *   - Algorithm 1: the outer loop (build the centroid index, assign, refine
+ *     c_j = sv(j)/|S_j|) is dkm_run / dkm_fit.
+ *
+ * Conventions (every function):
+ *   - Array arguments may be device pointers (cudaMalloc / torch CUDA
+ *     tensors) or host pointers (pageable or pinned); the library detects
+ *     which with cudaPointerGetAttributes and copies host data through its
+ *     own device buffers.  The caller owns every array it passes.
+ *   - Points are row-major n x d float32 (d = 2 or 3); centroids are
+ *     row-major k x d float32; labels are int32 in [0, k), in the caller's
+ *     original point order.
+ *   - Work is enqueued on dkm_options.stream (a cudaStream_t; NULL = the
+ *     legacy default stream).  Each call returns after its host-visible
+ *     outputs (sse, iterations, changed) are written; device outputs are
+ *     ready in stream order.
+ *   - No exception crosses the ABI.  Every function returns a dkm_status;
+ *     dkm_last_error() gives the message of the calling thread's last
+ *     failure.
+ *   - Ties go to the lowest centroid index; an empty cluster keeps its
+ *     previous centroid.
+ */
+#ifndef DKM_H_
+#define DKM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DKM_API __attribute__((visibility("default")))
+#else
+#define DKM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DKM_OK = 0,
+    DKM_EINVAL = 1,     /* bad argument, non-finite input, label out of range */
+    DKM_ENOMEM = 2,     /* device allocation failed, or the index cannot fit the budget */
+    DKM_ECUDA = 3,      /* a CUDA runtime call failed (message in dkm_last_error) */
+    DKM_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    DKM_EINTERNAL = 5   /* an internal consistency check failed */
+} dkm_status;
+
+enum {
+    DKM_ALGO_INDEXED = 0,   /* Morton tiles + centroid grid pruning (the method) */
+    DKM_ALGO_BRUTE = 1      /* plain Lloyd: every point against every centroid */
+};
+
+typedef struct {
+    /* Cap, in bytes, on the per-iteration centroid index (the grid's cell
+     * counters and buckets, both parities).  The planner coarsens the grid
+     * until it fits, like the paper's memory-tunable leaf capacity.
+     * 0 = default (64 MiB). */
+    size_t mem_budget_bytes;
+    /* Target grid cells per centroid before the budget cap (default 2.0). */
+    float cells_per_centroid;
+    /* DKM_ALGO_INDEXED (default) or DKM_ALGO_BRUTE. */
+    int algo;
+    /* dkm_run / dkm_fit: 1 = stop after the first assignment pass that
+     * changes no label (default); 0 = always run max_iter passes. */
+    int early_stop;
+    /* 1 = record per-kernel CUDA events, read back by dkm_last_timings. */
+    int profile;
+    /* cudaStream_t to enqueue on; NULL = legacy default stream. */
+    void* stream;
+} dkm_options;
+
+/* Grid plan for a point set (host-only arithmetic, no GPU needed). */
+typedef struct {
+    int dims[3];            /* cells per axis (dims[2] = 1 when d = 2) */
+    float cell;             /* cell edge length */
+    float origin[3];        /* low corner of the grid */
+    int bucket_cap;         /* centroid slots per cell before the overflow list */
+    int64_t cells;          /* dims[0]*dims[1]*dims[2] */
+    size_t index_bytes;     /* bytes of the per-iteration centroid index */
+    size_t scratch_bytes;   /* all device scratch a context of this size owns */
+} dkm_plan_info;
+
+typedef struct {
+    float setup_ms;         /* last dkm_setup: bbox, Morton sort, tile boxes */
+    float iterations_ms;    /* last dkm_run: all passes (graph launch) */
+    float search_ms;        /* mean per pass: per-block candidate search */
+    float assign_ms;        /* mean per pass: assignment + accumulation kernel */
+    float update_ms;        /* mean per pass: centroid update + grid rebuild */
+    float finalize_ms;      /* last dkm_run: label un-permute + final SSE */
+    int passes;             /* passes the timings cover */
+} dkm_timings;
+
+typedef struct {
+    double evals_per_point;     /* candidate distance evaluations per point, last pass */
+    double candidates_per_block;/* mean block candidate-list length, last pass */
+    int64_t fallback_blocks;    /* blocks whose candidate list overflowed, last pass */
+    int64_t grid_overflow;      /* centroids placed in the overflow list, last rebuild */
+    int passes;                 /* assignment passes of the last dkm_run */
+} dkm_stats;
+
+typedef struct dkm_ctx dkm_ctx;
+
+/* Fill *opts with the defaults above. */
+DKM_API void dkm_default_options(dkm_options* opts);
+
+/* Static string for a status code. */
+DKM_API const char* dkm_status_string(dkm_status s);
+
+/* Message of the calling thread's last failing call ("" if none). */
+DKM_API const char* dkm_last_error(void);
+
+/*
+ * Plan the centroid grid for n points of dimension d with bounding box
+ * [bbox_lo, bbox_hi] (d floats each) and k centroids, under opts'
+ * memory budget (Section V-A analog).  Pure host arithmetic.
+ * DKM_EINVAL on bad sizes; DKM_ENOMEM if even a single cell exceeds the
+ * budget.
+ */
+DKM_API dkm_status dkm_plan(int64_t n, int d, int k, const float* bbox_lo, const float* bbox_hi,
+                    const dkm_options* opts, dkm_plan_info* out);
+
+/*
+ * Create a context for n points of dimension d and k clusters, allocate
+ * its device scratch and build the point index (dkm_setup) from points
+ * (n x d).  The library keeps its own sorted copy; the caller may free
+ * points afterwards.  opts may be NULL (defaults).
+ * Errors: DKM_EINVAL (d not 2/3, n < 1, k < 1, k > n, null pointer,
+ * non-finite point), DKM_ENOMEM, DKM_ECUDA.  On error *out is NULL.
+ */
+DKM_API dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int k,
+                      const dkm_options* opts);
+
+/*
+ * Rebuild the point index (bounding box, Morton sort into tiles, tile
+ * boxes -- the analog of building the spatial-vector Ball-tree once,
+ * Algorithm 1 first step) for a new set of n x d points of the context's
+ * size.  Errors: DKM_EINVAL (null, non-finite), DKM_ECUDA.
+ */
+DKM_API dkm_status dkm_setup(dkm_ctx* ctx, const float* points);
+
+/*
+ * One assignment pass (Section II-A assignment step, pruned as in Section
+ * IV-A): labels[i] = index of the nearest of the k x d centroids.
+ * labels (n, original order) may be NULL.  sse_out (nullable) receives
+ * sum_i min_j ||p_i - c_j||^2 for these centroids.  changed_out (nullable)
+ * receives how many labels differ from this context's previous pass (all n
+ * on the first).  The per-cluster sums of this pass are kept for
+ * dkm_update(ctx, NULL, ...).
+ */
+DKM_API dkm_status dkm_assign(dkm_ctx* ctx, const float* centroids, int32_t* labels,
+                      double* sse_out, int64_t* changed_out);
+
+/*
+ * One update step (Algorithm 1 refine: c_j = mean of the points labelled
+ * j; an empty cluster keeps its centroid).  labels (n, original order):
+ * the labelling to average; NULL = the labels of the last dkm_assign on
+ * this context, whose sums are reused.  centroids_inout (k x d): the
+ * previous centroids on entry, the new ones on return.  counts (k,
+ * nullable) receives the cluster sizes.  DKM_EINVAL if a label is out of
+ * range (centroids_inout is then left unchanged) or if labels is NULL
+ * before any dkm_assign.
+ */
+DKM_API dkm_status dkm_update(dkm_ctx* ctx, const int32_t* labels, float* centroids_inout,
+                      int32_t* counts);
+
+/*
+ * Lloyd's loop on the context's points (Algorithm 1): up to max_iter
+ * passes of assignment + update, starting from init_centroids (k x d).
+ * With opts.early_stop the loop ends after the first pass that changes no
+ * label.  iterations_out = passes executed.  centroids_out (k x d) = the
+ * centroids after the last update; labels_out (n) = the last pass's
+ * labels; sse_out = SSE of those labels against centroids_out.
+ * max_iter = 0 labels the points against init_centroids (no update) and
+ * returns them unchanged.  Outputs other than iterations_out may be NULL.
+ */
+DKM_API dkm_status dkm_run(dkm_ctx* ctx, const float* init_centroids, int max_iter,
+                   float* centroids_out, int32_t* labels_out, int* iterations_out,
+                   double* sse_out);
+
+/*
+ * One-shot k-means: dkm_create + dkm_run + dkm_destroy.  opts may be NULL.
+ */
+DKM_API dkm_status dkm_fit(const float* points, int64_t n, int d, int k, const float* init_centroids,
+                   int max_iter, float* centroids_out, int32_t* labels_out,
+                   int* iterations_out, double* sse_out, const dkm_options* opts);
+
+/* Device bytes the context owns, and how many of them are the per-iteration
+ * centroid index.  Either pointer may be NULL. */
+DKM_API dkm_status dkm_query_memory(const dkm_ctx* ctx, size_t* device_bytes, size_t* index_bytes);
+
+/* Plan the context was built with. */
+DKM_API dkm_status dkm_get_plan(const dkm_ctx* ctx, dkm_plan_info* out);
+
+/* Timings of the last dkm_setup / dkm_run (needs opts.profile for the
+ * per-kernel means; otherwise those are 0). */
+DKM_API dkm_status dkm_last_timings(const dkm_ctx* ctx, dkm_timings* out);
+
+/* Pruning counters of the last pass (reads device counters; synchronises
+ * the context's stream). */
+DKM_API dkm_status dkm_last_stats(dkm_ctx* ctx, dkm_stats* out);
+
+/* Free the context and its device memory.  NULL is a no-op. */
+DKM_API void dkm_destroy(dkm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DKM_H_ */

@@ -1,0 +1,98 @@
+// dkm_host.h -- internal declarations shared by the libdkm translation units:
+// the kernel launchers (defined next to their kernels) and the context.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/dkm.h"
+#include "dkm_device.cuh"
+
+namespace dkm {
+
+// dkm_setup.cu
+cudaError_t launch_bbox(const float* p, int64_t n, int d, DevState* st, int which, int d_ctx,
+                        cudaStream_t s);
+cudaError_t launch_morton(const float* p, int64_t n, int d, const float* lo, float inv,
+                          uint32_t* keys, uint32_t* vals, cudaStream_t s);
+int64_t radix_sort_nb(int64_t n);
+cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits,
+                              uint32_t* counts, uint32_t* totals, int* final_buf, cudaStream_t s);
+cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,
+                          float* ys, float* zs, int64_t n_pad, cudaStream_t s);
+cudaError_t launch_boxes(const float* xs, const float* ys, const float* zs, int64_t n, int d,
+                         int n_blocks, float4* tbox, float4* bbox, cudaStream_t s);
+
+// dkm_iter.cu
+cudaError_t launch_reset_run(DevState* st, cudaStream_t s);
+cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const float* user_c,
+                             int insert, int par, int32_t* counts_out, cudaStream_t s);
+cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s);
+cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s);
+cudaError_t launch_collect(const IterArgs& A, int t, cudaStream_t s);
+cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
+                                const uint32_t* perm, cudaStream_t s);
+cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int32_t* labels_out,
+                            int do_sse, cudaStream_t s);
+cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s);
+
+}  // namespace dkm
+
+struct dkm_ctx {
+  int64_t n = 0;
+  int d = 0, k = 0;
+  dkm_options opts{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int n_blocks = 0, n_tiles = 0;
+  int64_t n_pad = 0;
+  int64_t max_cells = 0;       // grid capacity the arena was sized for
+  dkm_plan_info plan{};
+  dkm::Grid grid{};
+  float pbox_lo[3] = {0, 0, 0}, pbox_hi[3] = {0, 0, 0};
+  bool ready = false;          // the point index is valid
+  bool acc_valid = false;      // acc holds the sums of the last dkm_assign
+
+  // device arena
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  size_t index_bytes = 0;
+  float *xs = nullptr, *ys = nullptr, *zs = nullptr;
+  uint32_t* keys[2] = {nullptr, nullptr};
+  uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* perm = nullptr;    // sorted position -> original index
+  uint32_t *rs_counts = nullptr, *rs_totals = nullptr;
+  float4 *tbox = nullptr, *bbox = nullptr;
+  int32_t* lab = nullptr;
+  float4* cw = nullptr;
+  dkm::Acc* acc = nullptr;
+  dkm::Slot* slots = nullptr;
+  dkm::DevState* st = nullptr;
+  int* gcnt[2] = {nullptr, nullptr};
+  float4* gbkt[2] = {nullptr, nullptr};
+  float4* ovf[2] = {nullptr, nullptr};
+  int* ovf_cnt = nullptr;
+  float4* blist = nullptr;
+  int* bcnt = nullptr;
+  float* cstage = nullptr;     // k x d centroid staging
+  float* cstage2 = nullptr;    // k x d centroid output staging
+  int32_t* kstage = nullptr;   // k counts staging
+
+  // lazily allocated
+  double* sse_hist = nullptr;
+  unsigned long long* chg_hist = nullptr;
+  int hist_cap = 0;
+  float* pstage = nullptr;     // n x d, for host point input
+  int32_t* lstage = nullptr;   // n, for host label input / output
+
+  // cached iteration graph
+  cudaGraphExec_t gexec = nullptr;
+  int g_iters = -1, g_algo = -1, g_early = -1, g_profile = -1;
+  std::vector<cudaEvent_t> ev;        // per-pass events of the cached graph
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
+
+  dkm_timings timings{};
+};
