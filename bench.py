@@ -1,0 +1,365 @@
+"""Benchmark: indexed k-means on the 3D LiDAR-like workload (n = 1e7 float32
+points, k = 1e4, 30 fixed Lloyd iterations, seeded-permutation init).
+
+One step = the whole hot path on one batch: dkm_setup (bounding box, Morton
+sort into tiles, tile boxes) + dkm_run (30 passes of candidate search,
+assignment and update, then labels back to input order and the final SSE).
+value = n * iterations / step time (point-iterations per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (plain brute-force Lloyd) on a
+bounded sample of the same workload on the host cores.
+For N > 1 (torchrun) every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "point-iterations/s"
+WORKLOAD = dict(workload="lidar3d", n=10_000_000, d=3, k=10_000, iterations=30,
+                init="first k of a seeded permutation", seed=3,
+                l2="inputs larger than L2 (120 MB of points, 160 MB moved per pass)")
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes of one k_assign launch per point: read x, y, z (12 B) and
+# write the label (4 B); no previous-label read in fixed-iteration runs
+ASSIGN_BYTES_PER_POINT = 16
+# DRAM bytes (read + write) of one k_assign launch from the committed ncu
+# capture, valid only while the kernel source is unchanged
+NCU_TRAFFIC = None          # {"sha": ..., "bytes_per_launch": ...}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("dkm_iter.cu", "dkm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_02244_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="dkm_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(step_times_s, n: int, iters: int, world: int):
+    """Whole-job throughput: every rank processed n*iters point-iterations per
+    step; the job's step time is the slowest rank's."""
+    t = float(max(step_times_s))
+    return world * n * iters / t, t
+
+
+def load_workload():
+    from paper_2412_02244_gb300 import synth
+    return synth.lidar3d(seed=WORKLOAD["seed"], n=WORKLOAD["n"], k=WORKLOAD["k"],
+                         max_iter=WORKLOAD["iterations"])
+
+
+def cpu_sample_run(w, m: int, seed: int = 0):
+    """The oracle as it stands on a bounded sample: one Lloyd iteration
+    (brute-force FP64 assignment against all k centroids + update) of m
+    points drawn from the workload.  Returns (point-iterations/s, seconds,
+    threads)."""
+    import oracle
+    o = oracle.get()
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(w.n, size=m, replace=False)
+    sample = np.ascontiguousarray(w.points[idx])
+    t0 = time.perf_counter()
+    o.fit(sample, w.init.astype(np.float64), 1, early_stop=False)
+    dt = time.perf_counter() - t0
+    return m / dt, dt, o.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = load_workload()
+    m = args.ref_sample
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, dt, thr = cpu_sample_run(w, m, seed=s)
+        if s >= args.warmup:
+            vals.append((v, dt))
+    value = float(np.median([v for v, _ in vals]))
+    t_step = float(np.median([dt for _, dt in vals]))
+    sample = (f"one Lloyd iteration (FP64 brute-force assignment against all k=10000 "
+              f"centroids + update) of {m} points drawn from the n=1e7 workload, per step")
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": WORKLOAD, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def launches_per_step(iters: int) -> int:
+    # dkm_setup: reset_boxes, bbox, morton, 4 x (upsweep, scan, downsweep), gather, boxes
+    setup = 2 + 1 + 12 + 1 + 1
+    # dkm_run: centroid reset_boxes + bbox; graph: reset_run, prep, iters x (search, assign,
+    # centroids); finalize, collect, export
+    run = 2 + 2 + 3 * iters + 3
+    return setup + run
+
+
+def run_ours(args):
+    import torch
+    from paper_2412_02244_gb300 import build as b
+    b.build()
+    from paper_2412_02244_gb300 import dkm
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = load_workload()
+    n, d, k, iters = w.n, w.d, w.k, WORKLOAD["iterations"]
+    stream = torch.cuda.Stream(device=dev)
+    pts = torch.from_numpy(w.points).to(dev)
+    init = torch.from_numpy(w.init).to(dev)
+    C = torch.empty(k * d, dtype=torch.float32, device=dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    opts = dkm.dkm_default_options(early_stop=0, profile=int(args.profile),
+                                   stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ctx = dkm.dkm_create(pts, n, d, k, opts)
+
+    def step():
+        dkm.dkm_setup(ctx, pts)
+        return dkm.dkm_run(ctx, init, iters, C, lab)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    assign_ms, search_ms, update_ms, setup_ms = [], [], [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            it, sse = step()
+            if args.profile:
+                T = dkm.dkm_last_timings(ctx)
+                assign_ms.append(T.assign_ms)
+                search_ms.append(T.search_ms)
+                update_ms.append(T.update_ms)
+                setup_ms.append(T.setup_ms)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    times = [t_step]
+    if dist:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        times = [float(tt.item())]
+    value, t_job = aggregate(times, n, iters, ws)
+    stats = dkm.dkm_last_stats(ctx)
+
+    # end to end through the public API with host (pinned) buffers
+    pts_h = torch.from_numpy(w.points).pin_memory()
+    init_h = torch.from_numpy(w.init).pin_memory()
+    C_h = torch.empty(k * d, dtype=torch.float32).pin_memory()
+    lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    dkm.dkm_setup(ctx, pts_h)
+    dkm.dkm_run(ctx, init_h, iters, C_h, lab_h)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dkm.dkm_setup(ctx, pts_h)
+        dkm.dkm_run(ctx, init_h, iters, C_h, lab_h)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = ws * n * iters / t_e2e
+
+    # brute-force Lloyd on the same GPU, from the same converged centroids
+    brute = None
+    if rank == 0 and not args.no_brute:
+        ob = dkm.dkm_default_options(early_stop=0, profile=1, algo=dkm.DKM_ALGO_BRUTE,
+                                     stream=stream.cuda_stream)
+        cb = dkm.dkm_create(pts, n, d, k, ob)
+        Cb = torch.empty(k * d, dtype=torch.float32, device=dev)
+        lb = torch.empty(n, dtype=torch.int32, device=dev)
+        dkm.dkm_run(cb, C, 2, Cb, lb)
+        Tb = dkm.dkm_last_timings(cb)
+        oi = dkm.dkm_default_options(early_stop=0, profile=1, stream=stream.cuda_stream)
+        ci = dkm.dkm_create(pts, n, d, k, oi)
+        dkm.dkm_run(ci, C, 2, Cb, lb)
+        dkm.dkm_run(ci, C, 2, Cb, lb)
+        Ti = dkm.dkm_last_timings(ci)
+        per_b = Tb.search_ms + Tb.assign_ms + Tb.update_ms
+        per_i = Ti.search_ms + Ti.assign_ms + Ti.update_ms
+        brute = {"ms_per_iteration": per_b, "indexed_ms_per_iteration": per_i,
+                 "speedup_indexed_over_brute": per_b / per_i if per_i > 0 else None,
+                 "from": "converged centroids of the timed run, 2 passes each"}
+        cb.close()
+        ci.close()
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+    hbm, src = peaks()
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_job * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": WORKLOAD}
+    if args.profile and assign_ms:
+        a_ms = float(np.mean(assign_ms))
+        achieved = n * ASSIGN_BYTES_PER_POINT / (a_ms * 1e-3) / 1e9
+        traffic = None
+        if NCU_TRAFFIC and NCU_TRAFFIC.get("sha") == kernel_sha():
+            traffic = NCU_TRAFFIC["bytes_per_launch"]
+        line["roofline"] = {"bound": "hbm", "kernel": "k_assign", "achieved": achieved,
+                            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                            "peak_source": src, "traffic": traffic,
+                            "algorithmic_bytes_per_launch": n * ASSIGN_BYTES_PER_POINT,
+                            "launch_ms": a_ms}
+        per_iter = float(np.mean(search_ms) + np.mean(assign_ms) + np.mean(update_ms))
+        line["per_iteration"] = {"ms": per_iter, "search_ms": float(np.mean(search_ms)),
+                                 "assign_ms": a_ms, "update_ms": float(np.mean(update_ms)),
+                                 "point_iterations_per_s": n / (per_iter * 1e-3),
+                                 "hbm_frac_of_iteration": n * ASSIGN_BYTES_PER_POINT
+                                 / (per_iter * 1e-3) / 1e9 / hbm,
+                                 "setup_ms": float(np.mean(setup_ms))}
+    line["pruning"] = {"evals_per_point": stats.evals_per_point,
+                       "candidates_per_tile": stats.candidates_per_tile,
+                       "fallback_tiles": stats.fallback_tiles,
+                       "tiles": stats.tiles, "tile_level": stats.tile_level,
+                       "grid_overflow": stats.grid_overflow}
+    if brute:
+        line["brute_force"] = brute
+    line["e2e"] = {"value": e2e_value, "unit": METRIC,
+                   "h2d_bytes_per_step": n * d * 4 + k * d * 4,
+                   "d2h_bytes_per_step": n * 4 + k * d * 4, "steps": e2e_steps}
+    line["gpu_launches"] = launches_per_step(iters) * args.steps
+    line["clocks"] = clk.summary()
+    if ws == 1 and not args.no_cpu_baseline:
+        v, dt, thr = cpu_sample_run(w, args.cpu_sample)
+        line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle",
+                                "sample": f"one FP64 brute-force Lloyd iteration of "
+                                          f"{args.cpu_sample} sampled points against all "
+                                          f"k=10000 centroids ({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", type=int, default=1,
+                    help="record per-kernel CUDA events inside the run graph (roofline)")
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--ref-sample", type=int, default=500_000)
+    ap.add_argument("--no-brute", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -109,9 +109,11 @@ typedef struct {
 
 typedef struct {
     double evals_per_point;     /* candidate distance evaluations per point, last pass */
-    double candidates_per_block;/* mean block candidate-list length, last pass */
-    int64_t fallback_blocks;    /* blocks whose candidate list overflowed, last pass */
+    double candidates_per_tile; /* mean tile candidate-list length, last pass */
+    int64_t fallback_tiles;     /* tiles whose candidate list overflowed, last pass */
     int64_t grid_overflow;      /* centroids placed in the overflow list, last rebuild */
+    int64_t tiles;              /* tiles of the point index (<= 256 points each) */
+    int tile_level;             /* Morton level whose cubes bound the tiles */
     int passes;                 /* assignment passes of the last dkm_run */
 } dkm_stats;
 

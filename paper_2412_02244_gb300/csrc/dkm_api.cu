@@ -145,16 +145,22 @@ struct Layout {
 
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
-  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, bbox, lab, cw, acc,
-      slots, st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt, blist, bcnt, cstage, cstage2,
-      kstage, total;
+  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles, wcnt,
+      wbase, level_hist, lab, cw, acc, slots, st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt,
+      tlist, tcnt, cstage, cstage2, kstage, total;
 };
+
+int64_t windows_of(int64_t n) { return (n + kTilePts - 1) / kTilePts; }
+// Cube cuts add at most one tile per cube, and the tiling level is chosen so
+// that the cubes number at most an eighth of the windows.
+int64_t tiles_max_of(int64_t n) { return windows_of(n) + windows_of(n) / 8 + 2; }
 
 ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
   ArenaPlan P;
   Layout L;
   const int64_t nb = (n + kBlockPts - 1) / kBlockPts;
   const int64_t n_pad = nb * kBlockPts;
+  const int64_t nw = windows_of(n), tm = tiles_max_of(n);
   P.xs = L.take<float>(n_pad);
   P.ys = L.take<float>(n_pad);
   P.zs = L.take<float>(d == 3 ? n_pad : 1);
@@ -164,8 +170,12 @@ ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
   P.vals1 = L.take<uint32_t>(n);
   P.rs_counts = L.take<uint32_t>(256 * radix_sort_nb(n));
   P.rs_totals = L.take<uint32_t>(256);
-  P.tbox = L.take<float4>(2 * nb * kWarpsPerBlock);
-  P.bbox = L.take<float4>(2 * nb);
+  P.tbox = L.take<float4>(2 * tm);
+  P.tiles = L.take<int2>(tm);
+  P.n_tiles = L.take<int>(1);
+  P.wcnt = L.take<int>(nw);
+  P.wbase = L.take<int>(nw);
+  P.level_hist = L.take<unsigned long long>(kMaxLevels + 1);
   P.lab = L.take<int32_t>(n_pad);
   P.cw = L.take<float4>(k);
   P.acc = L.take<Acc>(k);
@@ -178,8 +188,8 @@ ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
   P.ovf0 = L.take<float4>(k);
   P.ovf1 = L.take<float4>(k);
   P.ovf_cnt = L.take<int>(2);
-  P.blist = L.take<float4>(nb * kMaxCand);
-  P.bcnt = L.take<int>(nb);
+  P.tlist = L.take<int>(tm * kTileCap);
+  P.tcnt = L.take<int>(tm);
   P.cstage = L.take<float>((size_t)k * d);
   P.cstage2 = L.take<float>((size_t)k * d);
   P.kstage = L.take<int32_t>(k);
@@ -192,13 +202,14 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   memset(&A, 0, sizeof(A));
   A.n = c->n;
   A.k = c->k;
-  A.n_blocks = c->n_blocks;
-  A.n_tiles = c->n_tiles;
+  A.n_windows = c->n_windows;
+  A.tiles_max = c->tiles_max;
+  A.n_tiles = c->n_tiles_dev;
+  A.tiles = c->tiles;
   A.xs = c->xs;
   A.ys = c->ys;
   A.zs = c->zs;
   A.tbox = c->tbox;
-  A.bbox = c->bbox;
   A.lab = c->lab;
   A.cw = c->cw;
   A.acc = c->acc;
@@ -211,13 +222,23 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
     A.ovf[p] = c->ovf[p];
   }
   A.ovf_cnt = c->ovf_cnt;
-  A.blist = c->blist;
-  A.bcnt = c->bcnt;
+  A.tlist = c->tlist;
+  A.tcnt = c->tcnt;
   A.sse_hist = c->sse_hist;
   A.chg_hist = c->chg_hist;
   A.track_changes = track_changes;
   A.early_stop = early_stop;
+  A.row_filter_min = c->row_filter_min;
   return A;
+}
+
+// Tuning knob, read once per context: DKM_ROW_FILTER_MIN (default 48).
+int env_int(const char* name, int def) {
+  const char* v = getenv(name);
+  if (!v || !*v) return def;
+  char* end = nullptr;
+  long x = strtol(v, &end, 10);
+  return (end && *end == 0) ? (int)x : def;
 }
 
 dkm_status check_ctx(const dkm_ctx* c) {
@@ -369,14 +390,14 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
     if ((e = launch_centroids(A, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream))) break;
     for (int t = 0; t < iters; ++t) {
       const int par = t & 1;
-      if (profile && (e = cudaEventRecord(c->ev[4 * t + 0], c->stream))) break;
+      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, cudaEventRecordExternal))) break;
       if (!brute && (e = launch_search(A, par, c->d, c->stream))) break;
-      if (profile && (e = cudaEventRecord(c->ev[4 * t + 1], c->stream))) break;
+      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 1], c->stream, cudaEventRecordExternal))) break;
       if ((e = launch_assign(A, c->d, brute, c->stream))) break;
-      if (profile && (e = cudaEventRecord(c->ev[4 * t + 2], c->stream))) break;
+      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, cudaEventRecordExternal))) break;
       const int insert = !brute && t + 1 < iters;
       if ((e = launch_centroids(A, 1, t, c->d, nullptr, insert, par ^ 1, nullptr, c->stream))) break;
-      if (profile && (e = cudaEventRecord(c->ev[4 * t + 3], c->stream))) break;
+      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, cudaEventRecordExternal))) break;
     }
   } while (0);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
@@ -486,14 +507,17 @@ dkm_status dkm_setup(dkm_ctx* c, const float* points) {
   if (plan.cells > c->max_cells) return fail(DKM_EINTERNAL, "grid plan exceeds the arena");
   plan.scratch_bytes = c->arena_bytes;
   c->plan = plan;
+  Grid g{};
   for (int a = 0; a < 3; ++a) {
-    c->grid.g0[a] = plan.origin[a];
-    c->grid.dims[a] = plan.dims[a];
+    g.g0[a] = plan.origin[a];
+    g.dims[a] = plan.dims[a];
   }
-  c->grid.inv_s = 1.0f / plan.cell;
-  c->grid.cap = plan.bucket_cap;
-  c->grid.cells = plan.cells;
-  if (c->gexec) destroy_graph(c);   // grid geometry is baked into the graph
+  g.inv_s = 1.0f / plan.cell;
+  g.cap = plan.bucket_cap;
+  g.cells = plan.cells;
+  // the grid geometry is baked into the cached graph: rebuild it only if it changed
+  if (memcmp(&g, &c->grid, sizeof(Grid)) != 0 && c->gexec) destroy_graph(c);
+  c->grid = g;
 
   // Morton keys on a cubic lattice over the bbox
   float emax = 0.f;
@@ -506,7 +530,27 @@ dkm_status dkm_setup(dkm_ctx* c, const float* points) {
                            c->stream));
   c->perm = c->vals[fin];
   DKM_CK(launch_gather(src, c->n, c->d, c->perm, c->xs, c->ys, c->zs, c->n_pad, c->stream));
-  DKM_CK(launch_boxes(c->xs, c->ys, c->zs, c->n, c->d, c->n_blocks, c->tbox, c->bbox, c->stream));
+  // Tiling level: the finest Morton level whose cubes cut the sorted order
+  // into at most n_windows / 8 pieces (so the cuts add at most 1/8 tiles).
+  DKM_CK(launch_levels(c->keys[fin], c->n, c->d, c->level_hist, c->stream));
+  unsigned long long hist[kMaxLevels + 1];
+  DKM_CK(cudaMemcpyAsync(hist, c->level_hist, sizeof(hist), cudaMemcpyDeviceToHost, c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  const int levels = c->d == 3 ? 10 : 15;
+  const unsigned long long seg_cap = (unsigned long long)std::max(1, c->n_windows / 8);
+  int level = 0;
+  unsigned long long segs = 1;
+  for (int l = 1; l <= levels; ++l) {
+    segs += hist[l];
+    if (segs > seg_cap) break;
+    level = l;
+  }
+  c->tile_level = level;
+  const int shift = c->d * (levels - level);
+  DKM_CK(launch_tiles(c->keys[fin], c->n, shift, c->n_windows, c->wcnt, c->wbase, c->n_tiles_dev,
+                      c->tiles, c->stream));
+  DKM_CK(launch_tile_boxes(c->xs, c->ys, c->zs, c->d, c->tiles, c->n_tiles_dev, c->tiles_max,
+                           c->tbox, c->stream));
   DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
   if (c->opts.profile) {
     DKM_CK(cudaEventRecord(c->ev_b, c->stream));
@@ -528,6 +572,7 @@ dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int 
   c->d = d;
   c->k = k;
   c->opts = resolve(opts);
+  c->row_filter_min = env_int("DKM_ROW_FILTER_MIN", 48);
   auto bail = [&](dkm_status s) {
     dkm_destroy(c);
     return s;
@@ -544,7 +589,8 @@ dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int 
     c->own_stream = true;
   }
   c->n_blocks = (int)((n + kBlockPts - 1) / kBlockPts);
-  c->n_tiles = c->n_blocks * kWarpsPerBlock;
+  c->n_windows = (int)windows_of(n);
+  c->tiles_max = (int)tiles_max_of(n);
   c->n_pad = (int64_t)c->n_blocks * kBlockPts;
   // arena sized for the largest grid this (k, budget) can plan
   {
@@ -575,7 +621,11 @@ dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int 
   c->rs_counts = (uint32_t*)(base + P.rs_counts);
   c->rs_totals = (uint32_t*)(base + P.rs_totals);
   c->tbox = (float4*)(base + P.tbox);
-  c->bbox = (float4*)(base + P.bbox);
+  c->tiles = (int2*)(base + P.tiles);
+  c->n_tiles_dev = (int*)(base + P.n_tiles);
+  c->wcnt = (int*)(base + P.wcnt);
+  c->wbase = (int*)(base + P.wbase);
+  c->level_hist = (unsigned long long*)(base + P.level_hist);
   c->lab = (int32_t*)(base + P.lab);
   c->cw = (float4*)(base + P.cw);
   c->acc = (Acc*)(base + P.acc);
@@ -588,8 +638,8 @@ dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int 
   c->ovf[0] = (float4*)(base + P.ovf0);
   c->ovf[1] = (float4*)(base + P.ovf1);
   c->ovf_cnt = (int*)(base + P.ovf_cnt);
-  c->blist = (float4*)(base + P.blist);
-  c->bcnt = (int*)(base + P.bcnt);
+  c->tlist = (int*)(base + P.tlist);
+  c->tcnt = (int*)(base + P.tcnt);
   c->cstage = (float*)(base + P.cstage);
   c->cstage2 = (float*)(base + P.cstage2);
   c->kstage = (int32_t*)(base + P.kstage);
@@ -759,8 +809,10 @@ dkm_status dkm_last_stats(dkm_ctx* c, dkm_stats* out) {
   DevState h;
   DKM_TRY(read_state(c, &h));
   out->evals_per_point = (double)h.last_evals / (double)c->n;
-  out->candidates_per_block = (double)h.last_cands / (double)c->n_blocks;
-  out->fallback_blocks = (int64_t)h.last_fallback;
+  out->candidates_per_tile = h.last_tiles ? (double)h.last_cands / (double)h.last_tiles : 0.0;
+  out->tiles = (int64_t)h.last_tiles;
+  out->tile_level = c->tile_level;
+  out->fallback_tiles = (int64_t)h.last_fallback;
   out->grid_overflow = (int64_t)h.grid_ovf;
   out->passes = h.passes;
   return DKM_OK;

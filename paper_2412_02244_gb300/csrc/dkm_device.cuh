@@ -9,23 +9,25 @@ namespace dkm {
 
 // ---------------------------------------------------------------------------
 // Work decomposition of the Morton-sorted points.
-//   row   = 64 consecutive points handled by one warp, two per lane, so the
-//           distance arithmetic runs on packed f32x2 pairs;
-//   tile  = 4 rows = 256 points = one warp's share; it owns a static AABB;
-//   block = 8 tiles = 2048 points = one CTA; it owns a static AABB and one
-//           candidate list per pass (the batch of Section IV-A).
+//   row    = 64 consecutive points handled by one warp, two per lane, so the
+//            distance arithmetic runs on packed f32x2 pairs;
+//   window = 4 rows = 256 aligned sorted positions;
+//   tile   = the points of one window that lie in one Morton cube of the
+//            chosen level (a window is cut where the cube changes); one
+//            warp per tile; it owns a static AABB and one candidate list per
+//            pass (the batch of Section IV-A).
 // ---------------------------------------------------------------------------
 constexpr int kRowPts = 64;
 constexpr int kRowsPerWarp = 4;
 constexpr int kTilePts = kRowPts * kRowsPerWarp;          // 256
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlockThreads = 32 * kWarpsPerBlock;        // 256
-constexpr int kBlockPts = kTilePts * kWarpsPerBlock;      // 2048
-constexpr int kMaxCand = 256;      // candidate-list capacity of one block
-constexpr int kChunk = 1024;       // centroids staged per round in brute force / fallback
+constexpr int kBlockPts = kTilePts * kWarpsPerBlock;      // 2048 (padding unit of the arrays)
+constexpr int kTileCap = 256;      // candidate-list capacity of one tile
 constexpr int kSlots = 256;        // spread counters (SSE, changed, evals)
 constexpr int kBucketCap = 8;      // centroid slots per grid cell
 constexpr int kMaxIterCap = 1 << 16;
+constexpr int kMaxLevels = 16;     // Morton levels (10 in 3D, 15 in 2D) + "never differs"
 
 // Keep a centroid as a candidate if mind^2(box, c) <= U^2 * kKeep.  The
 // factor covers the FP32 rounding of d^2, mind^2 and maxd^2 (each within
@@ -52,7 +54,7 @@ struct DevState {
   int err;               // internal error bits (kErr*)
   int label_err;         // dkm_update: a label outside [0, k)
   int pad0;
-  unsigned long long last_evals, last_cands, last_fallback, last_changed;
+  unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles;
   unsigned long long grid_ovf;   // centroids put in the overflow list, last rebuild
   double last_sse;               // SSE of the last pass (against its input centroids)
   double final_sse;              // SSE of the final labels against the final centroids
@@ -78,11 +80,12 @@ struct Grid {
 struct IterArgs {
   int64_t n;
   int k;
-  int n_blocks;
-  int n_tiles;
+  int n_windows;             // ceil(n / 256)
+  int tiles_max;             // launch bound on the tile count
+  const int* n_tiles;        // actual tile count (device)
+  const int2* tiles;         // per tile: [start, end) in sorted order
   const float* xs; const float* ys; const float* zs;   // sorted SoA points
   const float4* tbox;        // per tile: lo, hi (2 x float4)
-  const float4* bbox;        // per block: lo, hi
   int32_t* lab;              // sorted labels
   float4* cw;                // working centroids (x, y, z, id bits)
   Acc* acc;                  // per centroid
@@ -93,12 +96,13 @@ struct IterArgs {
   float4* gbkt[2];           // cells * cap entries
   float4* ovf[2];            // overflow list (k entries)
   int* ovf_cnt;              // [2]
-  float4* blist;             // n_blocks * kMaxCand sorted candidates
-  int* bcnt;                 // n_blocks list lengths (> kMaxCand = overflow)
+  int* tlist;                // tiles_max * kTileCap candidate ids (unordered)
+  int* tcnt;                 // per tile list length (> kTileCap = overflow)
   double* sse_hist;
   unsigned long long* chg_hist;
   int track_changes;         // read previous labels and count changes
   int early_stop;
+  int row_filter_min;        // tile lists longer than this are filtered again per row
 };
 
 // ---------------------------------------------------------------------------

@@ -22,8 +22,13 @@ cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, i
                               uint32_t* counts, uint32_t* totals, int* final_buf, cudaStream_t s);
 cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,
                           float* ys, float* zs, int64_t n_pad, cudaStream_t s);
-cudaError_t launch_boxes(const float* xs, const float* ys, const float* zs, int64_t n, int d,
-                         int n_blocks, float4* tbox, float4* bbox, cudaStream_t s);
+cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, unsigned long long* hist,
+                          cudaStream_t s);
+cudaError_t launch_tiles(const uint32_t* keys, int64_t n, int shift, int n_windows, int* wcnt,
+                         int* wbase, int* n_tiles, int2* tiles, cudaStream_t s);
+cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
+                              const int2* tiles, const int* n_tiles, int tiles_max, float4* tbox,
+                              cudaStream_t s);
 
 // dkm_iter.cu
 cudaError_t launch_reset_run(DevState* st, cudaStream_t s);
@@ -47,12 +52,16 @@ struct dkm_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
-  int n_blocks = 0, n_tiles = 0;
+  int n_blocks = 0;            // 2048-point padding blocks
+  int n_windows = 0;           // 256-point windows
+  int tiles_max = 0;           // capacity of the tile arrays
+  int tile_level = 0;          // Morton level whose cube boundaries cut tiles
   int64_t n_pad = 0;
   int64_t max_cells = 0;       // grid capacity the arena was sized for
   dkm_plan_info plan{};
   dkm::Grid grid{};
   float pbox_lo[3] = {0, 0, 0}, pbox_hi[3] = {0, 0, 0};
+  int row_filter_min = 48;     // per-row candidate filtering threshold
   bool ready = false;          // the point index is valid
   bool acc_valid = false;      // acc holds the sums of the last dkm_assign
 
@@ -65,7 +74,11 @@ struct dkm_ctx {
   uint32_t* vals[2] = {nullptr, nullptr};
   uint32_t* perm = nullptr;    // sorted position -> original index
   uint32_t *rs_counts = nullptr, *rs_totals = nullptr;
-  float4 *tbox = nullptr, *bbox = nullptr;
+  float4* tbox = nullptr;
+  int2* tiles = nullptr;
+  int* n_tiles_dev = nullptr;
+  int *wcnt = nullptr, *wbase = nullptr;
+  unsigned long long* level_hist = nullptr;
   int32_t* lab = nullptr;
   float4* cw = nullptr;
   dkm::Acc* acc = nullptr;
@@ -75,8 +88,8 @@ struct dkm_ctx {
   float4* gbkt[2] = {nullptr, nullptr};
   float4* ovf[2] = {nullptr, nullptr};
   int* ovf_cnt = nullptr;
-  float4* blist = nullptr;
-  int* bcnt = nullptr;
+  int* tlist = nullptr;
+  int* tcnt = nullptr;
   float* cstage = nullptr;     // k x d centroid staging
   float* cstage2 = nullptr;    // k x d centroid output staging
   int32_t* kstage = nullptr;   // k counts staging

@@ -2,18 +2,18 @@
 //
 // One Lloyd iteration (Algorithm 1 loop body) is three launches:
 //
-//   k_search   per block of 2048 Morton-sorted points: find every centroid
-//              that can be the nearest one of some point in the block's
-//              AABB (the batch pruning of Section IV-A) using the
-//              per-iteration centroid grid; write the list sorted by id.
-//   k_assign   per point: nearest candidate (ties -> lowest id), label
-//              store, and the per-cluster residual sums for the update,
-//              aggregated per warp by label and added with integer
-//              atomics (exact, order independent).  The BRUTE instance is
-//              plain Lloyd: every point against every centroid.
+//   k_search     per tile (<= 256 Morton-sorted points inside one Morton
+//                cube): every centroid that can be the nearest one of some
+//                point in the tile's AABB (the batch pruning of Section
+//                IV-A), found through the per-iteration centroid grid.
+//   k_assign     per point: nearest candidate (ties -> lowest id), label
+//                store, and the per-cluster residual sums for the update,
+//                aggregated per warp by label and added with integer
+//                atomics (exact, order independent).  The BRUTE instance is
+//                plain Lloyd: every point against every centroid.
 //   k_centroids  refine c_j = c_j + sum(p - c_j)/|S_j| (= the cluster
-//              mean; an empty cluster keeps c_j) and rebuild the centroid
-//              grid for the next pass.
+//                mean; an empty cluster keeps c_j) and rebuild the centroid
+//                grid for the next pass.
 //
 // Distances: d^2 = fma(dz, dz, fma(dy, dy, dx*dx)), dx = p + (-c), each
 // step rounded to nearest in FP32; the same expression in every kernel, so
@@ -73,6 +73,7 @@ __device__ void collect_slots(const IterArgs& A, int t) {
     A.st->last_evals = tot[2];
     A.st->last_cands = tot[3];
     A.st->last_fallback = tot[4];
+    A.st->last_tiles = (unsigned long long)(*A.n_tiles);
     if (t >= 0) {
       A.sse_hist[t] = sse;
       A.chg_hist[t] = tot[1];
@@ -138,8 +139,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
     int cz = d == 3 ? cell_coord(c.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
     long long cell = ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
     int slot = atomicAdd(&A.gcnt[par][cell], 1);
-    if (slot < G.cap) {
-      A.gbkt[par][cell * G.cap + slot] = c;
+    if (slot < kBucketCap) {
+      A.gbkt[par][cell * kBucketCap + slot] = c;
     } else {
       int o = atomicAdd(&A.ovf_cnt[par], 1);
       A.ovf[par][o] = c;
@@ -149,18 +150,18 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
 }
 
 // ---------------------------------------------------------------------------
-// k_search: one warp per block of 2048 points.
-//   phase A: U^2 = min over centroids in the block's own cells (growing
-//            rings if empty) of maxd^2(block box, c) -- any centroid gives
+// k_search: one warp per tile.
+//   phase A: U^2 = min over centroids in the tile's own cells (growing
+//            rings if empty) of maxd^2(tile box, c) -- any centroid gives
 //            an upper bound on every point's nearest distance;
-//   phase B: every centroid with mind^2(block box, c) <= U^2 * kKeep, found
+//   phase B: every centroid with mind^2(tile box, c) <= U^2 * kKeep, found
 //            in the cells overlapping the box grown by U, plus the
 //            overflow list.  The true nearest centroid of each point in the
 //            box always passes (its distance is <= the distance to the
-//            U-defining centroid <= U), which is the ball-node test of
-//            Section II-B / IV-A with boxes in place of balls.
-// The list is written sorted by centroid id, so a strict < scan gives the
-// lowest index on ties.
+//            U-defining centroid <= U): the ball-node test of Section II-B /
+//            IV-A with boxes in place of balls.
+// The list is written unordered; k_assign picks the lexicographic minimum
+// of (d^2, id), which does not depend on the order.
 // ---------------------------------------------------------------------------
 constexpr int kSearchWarps = 8;
 
@@ -168,8 +169,7 @@ __device__ __forceinline__ long long cell_index(const Grid& G, int cx, int cy, i
   return ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
 }
 
-__global__ void __launch_bounds__(32 * kSearchWarps) k_search(IterArgs A, int par, int d) {
-  __shared__ float4 s_list[kSearchWarps][kMaxCand];
+__global__ void __launch_bounds__(32 * kSearchWarps, 3) k_search(IterArgs A, int par, int d) {
   if (A.early_stop && A.st->done) return;
   // clear the other parity's grid for the next rebuild (nobody reads it now)
   {
@@ -179,14 +179,18 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(IterArgs A, int pa
     if (g == 0) A.ovf_cnt[par ^ 1] = 0;
   }
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int b = blockIdx.x * kSearchWarps + wl;
-  if (b >= A.n_blocks) return;
+  const int t = blockIdx.x * kSearchWarps + wl;
+  if (t >= A.tiles_max || t >= *A.n_tiles) return;
+  int* __restrict__ out = A.tlist + (int64_t)t * kTileCap;
   const Grid G = A.grid;
-  const float4 lo = A.bbox[2 * b], hi = A.bbox[2 * b + 1];
+  const float4 lo = A.tbox[2 * t], hi = A.tbox[2 * t + 1];
   const int* __restrict__ gcnt = A.gcnt[par];
   const float4* __restrict__ gbkt = A.gbkt[par];
   const int n_ovf = A.ovf_cnt[par];
   const float4* __restrict__ ovf = A.ovf[par];
+  // a range of more than k / 4 cells costs more than reading every centroid
+  // once, so large ranges scan the flat centroid array instead
+  const long long flat_cells = (long long)(A.k / 4) + 32;
 
   int clo[3], chi[3];
   clo[0] = cell_coord(lo.x, G.g0[0], G.inv_s, G.dims[0]);
@@ -208,19 +212,30 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(IterArgs A, int pa
       whole = whole && rlo[a] == 0 && rhi[a] == G.dims[a] - 1;
       ncell *= (long long)(rhi[a] - rlo[a] + 1);
     }
-    const int nx = rhi[0] - rlo[0] + 1, ny = rhi[1] - rlo[1] + 1;
     float m = INFINITY;
+    if (ncell > flat_cells) {
+      for (int j = lane; j < A.k; j += 32) {
+        const float4 c = A.cw[j];
+        m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
+      }
+      u2 = warp_min_nonneg(m);
+      break;
+    }
+    const int nx = rhi[0] - rlo[0] + 1, ny = rhi[1] - rlo[1] + 1;
     for (long long q = lane; q < ncell; q += 32) {
       int cx = rlo[0] + (int)(q % nx);
       long long r = q / nx;
       int cy = rlo[1] + (int)(r % ny);
       int cz = rlo[2] + (int)(r / ny);
       long long cell = cell_index(G, cx, cy, cz);
-      int cnt = min(gcnt[cell], G.cap);
-      for (int e = 0; e < cnt; ++e) {
-        float4 c = gbkt[cell * G.cap + e];
-        m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
-      }
+      int cnt = min(gcnt[cell], kBucketCap);
+      float4 e[kBucketCap];
+#pragma unroll
+      for (int i = 0; i < kBucketCap; ++i)
+        if (i < cnt) e[i] = gbkt[cell * kBucketCap + i];
+#pragma unroll
+      for (int i = 0; i < kBucketCap; ++i)
+        if (i < cnt) m = fminf(m, maxd2(lo, hi, e[i].x, e[i].y, e[i].z, d));
     }
     for (int q = lane; q < n_ovf; q += 32) {
       float4 c = ovf[q];
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(IterArgs A, int pa
   }
   if (!(u2 < INFINITY)) {   // no centroid anywhere: cannot happen for k >= 1
     if (lane == 0) {
-      A.bcnt[b] = 0;
+      A.tcnt[t] = 0;
       atomicOr(&A.st->err, kErrNoCentroid);
     }
     return;
@@ -253,73 +268,96 @@ __global__ void __launch_bounds__(32 * kSearchWarps) k_search(IterArgs A, int pa
   const long long ncell = (long long)nx * ny * (rhi[2] - rlo[2] + 1);
   const unsigned lt = (1u << lane) - 1u;
   int count = 0;
-  for (long long q0 = 0; q0 < ncell; q0 += 32) {
-    long long q = q0 + lane;
-    long long cell = 0;
-    int cnt = 0;
-    if (q < ncell) {
-      int cx = rlo[0] + (int)(q % nx);
-      long long r = q / nx;
-      int cy = rlo[1] + (int)(r % ny);
-      int cz = rlo[2] + (int)(r / ny);
-      cell = cell_index(G, cx, cy, cz);
-      cnt = min(gcnt[cell], G.cap);
-    }
-    const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-    for (int e = 0; e < cmax; ++e) {
+  if (ncell > flat_cells) {
+    // every centroid once; the overflow list is then redundant
+    for (int j0 = 0; j0 < A.k; j0 += 32) {
+      const int j = j0 + lane;
       float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
       bool keep = false;
-      if (e < cnt) {
-        c = gbkt[cell * G.cap + e];
+      if (j < A.k) {
+        c = A.cw[j];
         keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k;
       }
       unsigned bal = __ballot_sync(0xffffffffu, keep);
       int pos = count + __popc(bal & lt);
-      if (keep && pos < kMaxCand) s_list[wl][pos] = c;
+      if (keep && pos < kTileCap) out[pos] = __float_as_int(c.w);
+      count += __popc(bal);
+    }
+  } else {
+    for (long long q0 = 0; q0 < ncell; q0 += 32) {
+      long long q = q0 + lane;
+      long long cell = 0;
+      int cnt = 0;
+      if (q < ncell) {
+        int cx = rlo[0] + (int)(q % nx);
+        long long r = q / nx;
+        int cy = rlo[1] + (int)(r % ny);
+        int cz = rlo[2] + (int)(r / ny);
+        cell = cell_index(G, cx, cy, cz);
+        cnt = min(gcnt[cell], kBucketCap);
+      }
+      float4 e[kBucketCap];
+#pragma unroll
+      for (int i = 0; i < kBucketCap; ++i)
+        if (i < cnt) e[i] = gbkt[cell * kBucketCap + i];
+      const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+#pragma unroll
+      for (int i = 0; i < kBucketCap; ++i) {
+        if (i >= cmax) break;
+        const bool keep = i < cnt && mind2(lo, hi, e[i].x, e[i].y, e[i].z, d) <= u2k;
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int pos = count + __popc(bal & lt);
+        if (keep && pos < kTileCap) out[pos] = __float_as_int(e[i].w);
+        count += __popc(bal);
+      }
+    }
+    for (int q0 = 0; q0 < n_ovf; q0 += 32) {
+      int q = q0 + lane;
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      bool keep = false;
+      if (q < n_ovf) {
+        c = ovf[q];
+        keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k;
+      }
+      unsigned bal = __ballot_sync(0xffffffffu, keep);
+      int pos = count + __popc(bal & lt);
+      if (keep && pos < kTileCap) out[pos] = __float_as_int(c.w);
       count += __popc(bal);
     }
   }
-  for (int q0 = 0; q0 < n_ovf; q0 += 32) {
-    int q = q0 + lane;
-    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool keep = false;
-    if (q < n_ovf) {
-      c = ovf[q];
-      keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k;
-    }
-    unsigned bal = __ballot_sync(0xffffffffu, keep);
-    int pos = count + __popc(bal & lt);
-    if (keep && pos < kMaxCand) s_list[wl][pos] = c;
-    count += __popc(bal);
-  }
-  __syncwarp();
-  if (count <= kMaxCand) {
-    float4* out = A.blist + (int64_t)b * kMaxCand;
-    for (int i = lane; i < count; i += 32) {
-      float4 c = s_list[wl][i];
-      int id = __float_as_int(c.w);
-      int rank = 0;
-      for (int j2 = 0; j2 < count; ++j2) rank += __float_as_int(s_list[wl][j2].w) < id;
-      out[rank] = c;
-    }
-  }
   if (lane == 0) {
-    A.bcnt[b] = count;
-    Slot& s = A.slots[b & (kSlots - 1)];
+    A.tcnt[t] = count;
+    Slot& s = A.slots[t & (kSlots - 1)];
     red_add_u64(&s.cands, (unsigned long long)count);
-    if (count > kMaxCand) red_add_u64(&s.fallback, 1ull);
+    if (count > kTileCap) red_add_u64(&s.fallback, 1ull);
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_assign<D, BRUTE>: one CTA per block, one warp per tile of 4 rows x 64
-// points, two points per lane evaluated as packed f32x2.
+// k_assign<D, BRUTE>: one warp per tile of 4 rows x 64 points, two points
+// per lane evaluated as packed f32x2.  Warps are independent (no CTA-wide
+// barrier): each stages its own candidate list in shared memory.
 // ---------------------------------------------------------------------------
 template <int D>
 struct Pts {
   float2 x[kRowsPerWarp], y[kRowsPerWarp], z[kRowsPerWarp];
 };
 
+// Keep (s, id) if it is lexicographically smaller than (best, bid): the
+// nearest centroid, ties to the lowest index, whatever order the
+// candidates arrive in.  s >= 0, so its bit pattern orders like its value
+// and the pair compares as one 64-bit key.
+__device__ __forceinline__ void take_min(float s, int id, float& best, int& bid) {
+  const unsigned long long key = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)id;
+  const unsigned long long cur =
+      ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)bid;
+  if (key < cur) {
+    best = s;
+    bid = id;
+  }
+}
+
+// all rows of the tile against candidates s_c[idx[j]] (idx == nullptr: s_c[j])
 template <int D>
 __device__ __forceinline__ void eval_list(const float4* __restrict__ s_c,
                                           const unsigned short* __restrict__ idx, int m,
@@ -342,38 +380,74 @@ __device__ __forceinline__ void eval_list(const float4* __restrict__ s_c,
         float2 dz = __fadd2_rn(P.z[r], nz);
         s = __ffma2_rn(dz, dz, s);
       }
-      if (s.x < best[r].x) { best[r].x = s.x; bid[r].x = id; }
-      if (s.y < best[r].y) { best[r].y = s.y; bid[r].y = id; }
+      take_min(s.x, id, best[r].x, bid[r].x);
+      take_min(s.y, id, best[r].y, bid[r].y);
     }
   }
 }
 
-// Tile filter: U^2 of the tile box over the list, then the ids of the list
-// entries that can be some point's nearest (ascending positions, so the
-// filtered list stays sorted by id).  u2_run carries the bound across
-// chunks (fallback path).  Returns the filtered length.
+// one row (64 points, two per lane) against candidates s_c[idx[j]]
 template <int D>
-__device__ __forceinline__ int filter_tile(const float4* __restrict__ s_c, int q, float4 tlo,
-                                           float4 thi, unsigned short* __restrict__ out,
-                                           float& u2_run) {
-  const int lane = threadIdx.x & 31;
-  float m = INFINITY;
-  for (int j = lane; j < q; j += 32) {
-    float4 c = s_c[j];
-    m = fminf(m, maxd2(tlo, thi, c.x, c.y, c.z, D));
+__device__ __forceinline__ void eval_row(const float4* __restrict__ s_c,
+                                         const unsigned short* __restrict__ idx, int m, float2 px,
+                                         float2 py, float2 pz, float2& best, int2& bid) {
+#pragma unroll 4
+  for (int j = 0; j < m; ++j) {
+    const float4 c = s_c[idx[j]];
+    const int id = __float_as_int(c.w);
+    float2 dx = __fadd2_rn(px, make_float2(-c.x, -c.x));
+    float2 dy = __fadd2_rn(py, make_float2(-c.y, -c.y));
+    float2 s = __fmul2_rn(dx, dx);
+    s = __ffma2_rn(dy, dy, s);
+    if (D == 3) {
+      float2 dz = __fadd2_rn(pz, make_float2(-c.z, -c.z));
+      s = __ffma2_rn(dz, dz, s);
+    }
+    take_min(s.x, id, best.x, bid.x);
+    take_min(s.y, id, best.y, bid.y);
   }
-  u2_run = fminf(u2_run, warp_min_nonneg(m));
-  const float u2k = u2_run * kKeep;
+}
+
+// AABB of one row's valid points (warp-wide, identical on every lane).
+__device__ __forceinline__ void row_box(float2 px, float2 py, float2 pz, bool va, bool vb,
+                                        float4& lo, float4& hi) {
+  const float inf = INFINITY;
+  float mnx = fminf(va ? px.x : inf, vb ? px.y : inf), mxx = fmaxf(va ? px.x : -inf, vb ? px.y : -inf);
+  float mny = fminf(va ? py.x : inf, vb ? py.y : inf), mxy = fmaxf(va ? py.x : -inf, vb ? py.y : -inf);
+  float mnz = fminf(va ? pz.x : inf, vb ? pz.y : inf), mxz = fmaxf(va ? pz.x : -inf, vb ? pz.y : -inf);
+  lo.x = float_of(__reduce_min_sync(0xffffffffu, ord_of(mnx)));
+  lo.y = float_of(__reduce_min_sync(0xffffffffu, ord_of(mny)));
+  lo.z = float_of(__reduce_min_sync(0xffffffffu, ord_of(mnz)));
+  hi.x = float_of(__reduce_max_sync(0xffffffffu, ord_of(mxx)));
+  hi.y = float_of(__reduce_max_sync(0xffffffffu, ord_of(mxy)));
+  hi.z = float_of(__reduce_max_sync(0xffffffffu, ord_of(mxz)));
+  lo.w = hi.w = 0.f;
+}
+
+// Indices of the list entries s_c[0..m) that can hold the nearest centroid
+// of some point inside [lo, hi] (same bound as k_search with this box).
+// u2_in caps the bound (INFINITY = none); returns the count.
+template <int D>
+__device__ __forceinline__ int filter_box(const float4* __restrict__ s_c, int m, float4 lo,
+                                          float4 hi, float u2_in,
+                                          unsigned short* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  float u = u2_in;
+  for (int j = lane; j < m; j += 32) {
+    const float4 c = s_c[j];
+    u = fminf(u, maxd2(lo, hi, c.x, c.y, c.z, D));
+  }
+  const float u2k = warp_min_nonneg(u) * kKeep;
   const unsigned lt = (1u << lane) - 1u;
   int cnt = 0;
-  for (int j0 = 0; j0 < q; j0 += 32) {
-    int j = j0 + lane;
+  for (int j0 = 0; j0 < m; j0 += 32) {
+    const int j = j0 + lane;
     bool keep = false;
-    if (j < q) {
-      float4 c = s_c[j];
-      keep = mind2(tlo, thi, c.x, c.y, c.z, D) <= u2k;
+    if (j < m) {
+      const float4 c = s_c[j];
+      keep = mind2(lo, hi, c.x, c.y, c.z, D) <= u2k;
     }
-    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (keep) out[cnt + __popc(bal & lt)] = (unsigned short)j;
     cnt += __popc(bal);
   }
@@ -445,38 +519,44 @@ __device__ __forceinline__ long long row_sse(float d2a, float d2b, bool va, bool
   return rescale((long long)s, s2, s_sse);
 }
 
-__device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t tile_base,
-                                            float2 (&x)[kRowsPerWarp], float2 (&y)[kRowsPerWarp],
-                                            float2 (&z)[kRowsPerWarp], bool (&va)[kRowsPerWarp],
-                                            bool (&vb)[kRowsPerWarp]) {
+// The 4 rows of a 256-window starting at `base` (always inside the padded
+// arrays); a point is valid if its sorted index lies in [vlo, vhi).
+__device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t base, int64_t vlo,
+                                            int64_t vhi, float2 (&x)[kRowsPerWarp],
+                                            float2 (&y)[kRowsPerWarp], float2 (&z)[kRowsPerWarp],
+                                            bool (&va)[kRowsPerWarp], bool (&vb)[kRowsPerWarp]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    int64_t i = tile_base + r * kRowPts + 2 * lane;
-    // arrays are padded to a whole block, so the pair load is always in bounds
+    int64_t i = base + r * kRowPts + 2 * lane;
     x[r] = *reinterpret_cast<const float2*>(A.xs + i);
     y[r] = *reinterpret_cast<const float2*>(A.ys + i);
     z[r] = D == 3 ? *reinterpret_cast<const float2*>(A.zs + i) : make_float2(0.f, 0.f);
-    va[r] = i < A.n;
-    vb[r] = i + 1 < A.n;
+    va[r] = i >= vlo && i < vhi;
+    vb[r] = i + 1 >= vlo && i + 1 < vhi;
   }
 }
 
 template <int D, bool BRUTE>
-__global__ void __launch_bounds__(kBlockThreads) k_assign(IterArgs A) {
-  __shared__ float4 s_c[kChunk];
-  __shared__ unsigned short s_w[kWarpsPerBlock][kChunk];
+__global__ void __launch_bounds__(kBlockThreads, 3) k_assign(IterArgs A) {
+  __shared__ float4 s_c[kWarpsPerBlock][kTileCap];
+  __shared__ unsigned short s_r[kWarpsPerBlock][kTileCap];
   if (A.early_stop && A.st->done) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int b = blockIdx.x;
-  const int64_t tile = (int64_t)b * kWarpsPerBlock + w;
-  const int64_t tile_base = tile * kTilePts;
-  const bool tile_live = tile_base < A.n;
-  if (b == 0 && threadIdx.x == 0) atomicAdd(&A.st->passes, 1);
+  const int t = blockIdx.x * kWarpsPerBlock + w;
+  if (t == 0 && lane == 0) atomicAdd(&A.st->passes, 1);
+  if (t >= A.tiles_max || t >= *A.n_tiles) return;   // warp-level exit, no CTA barrier below
+  const int2 se = A.tiles[t];
+  const int64_t base = (int64_t)(se.x / kTilePts) * kTilePts;
 
   Pts<D> P;
   bool va[kRowsPerWarp], vb[kRowsPerWarp];
-  load_points(A, D, tile_base, P.x, P.y, P.z, va, vb);
+  load_points(A, D, base, se.x, se.y, P.x, P.y, P.z, va, vb);
+  int nv_row[kRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+    nv_row[r] = __popc(__ballot_sync(0xffffffffu, va[r])) + __popc(__ballot_sync(0xffffffffu, vb[r]));
+  const int nv_tile = se.y - se.x;
 
   float2 best[kRowsPerWarp];
   int2 bid[kRowsPerWarp];
@@ -485,60 +565,88 @@ __global__ void __launch_bounds__(kBlockThreads) k_assign(IterArgs A) {
     best[r] = make_float2(INFINITY, INFINITY);
     bid[r] = make_int2(0, 0);
   }
-  unsigned long long evals = 0;
-  float4 tlo = make_float4(0.f, 0.f, 0.f, 0.f), thi = tlo;
-  if (!BRUTE && tile_live) {
-    tlo = A.tbox[2 * tile];
-    thi = A.tbox[2 * tile + 1];
-  }
-  bool chunked = BRUTE;
-  if (!BRUTE) {
-    const int q = A.bcnt[b];
-    if (q <= kMaxCand) {
-      const float4* src = A.blist + (int64_t)b * kMaxCand;
-      for (int i = threadIdx.x; i < q; i += kBlockThreads) s_c[i] = src[i];
-      __syncthreads();
-      if (tile_live) {
-        float u2 = INFINITY;
-        int m = filter_tile<D>(s_c, q, tlo, thi, s_w[w], u2);
-        if (m == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
-        eval_list<D>(s_c, s_w[w], m, P, best, bid);
-        evals += (unsigned long long)m;
+  unsigned long long evals = 0;   // point x candidate evaluations of this warp
+  float4* __restrict__ sc = s_c[w];
+  unsigned short* __restrict__ sr = s_r[w];
+  if (BRUTE) {
+    for (int c0 = 0; c0 < A.k; c0 += kTileCap) {
+      const int m = min(kTileCap, A.k - c0);
+      __syncwarp();
+      for (int i = lane; i < m; i += 32) sc[i] = A.cw[c0 + i];
+      __syncwarp();
+      eval_list<D>(sc, nullptr, m, P, best, bid);
+    }
+    evals = (unsigned long long)A.k * nv_tile;
+  } else {
+    const int q = A.tcnt[t];
+    if (q <= kTileCap) {
+      const int* src = A.tlist + (int64_t)t * kTileCap;
+      for (int i = lane; i < q; i += 32) sc[i] = __ldg(&A.cw[src[i]]);
+      __syncwarp();
+      if (q == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
+      if (q > A.row_filter_min) {
+        // long list: narrow it again per row of 64 points
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r) {
+          if (nv_row[r] == 0) continue;
+          float4 rlo, rhi;
+          row_box(P.x[r], P.y[r], P.z[r], va[r], vb[r], rlo, rhi);
+          const int mr = filter_box<D>(sc, q, rlo, rhi, INFINITY, sr);
+          eval_row<D>(sc, sr, mr, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
+          evals += (unsigned long long)mr * nv_row[r];
+        }
+      } else {
+        eval_list<D>(sc, nullptr, q, P, best, bid);
+        evals = (unsigned long long)q * nv_tile;
       }
     } else {
-      chunked = true;
-    }
-  }
-  if (chunked) {
-    float u2 = INFINITY;
-    for (int c0 = 0; c0 < A.k; c0 += kChunk) {
-      const int m = min(kChunk, A.k - c0);
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += kBlockThreads) s_c[i] = A.cw[c0 + i];
-      __syncthreads();
-      if (tile_live) {
-        if (BRUTE) {
-          eval_list<D>(s_c, nullptr, m, P, best, bid);
-          evals += (unsigned long long)m;
-        } else {
-          int mm = filter_tile<D>(s_c, m, tlo, thi, s_w[w], u2);
-          eval_list<D>(s_c, s_w[w], mm, P, best, bid);
-          evals += (unsigned long long)mm;
+      // The list overflowed: take the tile bound over every centroid first,
+      // then stream every centroid once, keep the ones that pass the bound
+      // in shared memory and evaluate them whenever the buffer fills.
+      const float4 tlo = A.tbox[2 * t], thi = A.tbox[2 * t + 1];
+      float u = INFINITY;
+#pragma unroll 8
+      for (int j = lane; j < A.k; j += 32) {
+        const float4 c = __ldg(&A.cw[j]);
+        u = fminf(u, maxd2(tlo, thi, c.x, c.y, c.z, D));
+      }
+      const float u2k = warp_min_nonneg(u) * kKeep;
+      const unsigned lt = (1u << lane) - 1u;
+      int cnt = 0;
+      for (int j0 = 0; j0 < A.k; j0 += 4 * 32) {
+        float4 c[4];
+#pragma unroll
+        for (int b4 = 0; b4 < 4; ++b4) {
+          const int j = j0 + b4 * 32 + lane;
+          c[b4] = j < A.k ? __ldg(&A.cw[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int b4 = 0; b4 < 4; ++b4) {
+          const int j = j0 + b4 * 32 + lane;
+          const bool keep = j < A.k && mind2(tlo, thi, c[b4].x, c[b4].y, c[b4].z, D) <= u2k;
+          const unsigned bal = __ballot_sync(0xffffffffu, keep);
+          if (keep) sc[cnt + __popc(bal & lt)] = c[b4];
+          cnt += __popc(bal);
+        }
+        if (cnt > kTileCap - 4 * 32 || j0 + 4 * 32 >= A.k) {
+          __syncwarp();
+          eval_list<D>(sc, nullptr, cnt, P, best, bid);
+          evals += (unsigned long long)cnt * nv_tile;
+          cnt = 0;
+          __syncwarp();
         }
       }
     }
   }
-  if (!tile_live) return;
 
   int s_glob, s_sse;
   fixed_exponents(A.st, A.n, &s_glob, &s_sse);
   long long sse = 0;
   int changed = 0;
-  int nvalid = 0;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    const int64_t i = tile_base + r * kRowPts + 2 * lane;
-    if (tile_base + r * kRowPts >= A.n) break;   // warp-uniform
+    if (nv_row[r] == 0) continue;   // warp-uniform
+    const int64_t i = base + r * kRowPts + 2 * lane;
     const int la = bid[r].x, lb = bid[r].y;
     if (A.track_changes) {
       int pa = va[r] ? A.lab[i] : la, pb = vb[r] ? A.lab[i + 1] : lb;
@@ -548,42 +656,45 @@ __global__ void __launch_bounds__(kBlockThreads) k_assign(IterArgs A) {
       *reinterpret_cast<int2*>(A.lab + i) = make_int2(la, lb);
     } else if (va[r]) {
       A.lab[i] = la;
+    } else if (vb[r]) {
+      A.lab[i + 1] = lb;
     }
-    nvalid += (int)va[r] + (int)vb[r];
     sse += row_sse(best[r].x, best[r].y, va[r], vb[r], s_sse);
     accumulate_row(A, D, P.x[r], P.y[r], P.z[r], la, lb, va[r], vb[r], s_glob);
   }
   changed = __reduce_add_sync(0xffffffffu, changed);
-  nvalid = __reduce_add_sync(0xffffffffu, nvalid);
   if (lane == 0) {
-    Slot& s = A.slots[tile & (kSlots - 1)];
+    Slot& s = A.slots[t & (kSlots - 1)];
     red_add_u64(&s.sse, (unsigned long long)sse);
     if (changed) red_add_u64(&s.changed, (unsigned long long)changed);
-    red_add_u64(&s.evals, evals * (unsigned long long)nvalid);
+    red_add_u64(&s.evals, evals);
   }
 }
 
 // ---------------------------------------------------------------------------
 // k_accum_labels: residual sums for a caller-given labelling (dkm_update).
+// One warp per tile, grouped exactly like k_assign, so both produce the same
+// sums bit for bit for the same labels.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
                                                                const int32_t* __restrict__ ulab,
                                                                const uint32_t* __restrict__ perm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  const int64_t tile_base = tile * kTilePts;
-  if (tile_base >= A.n) return;
+  const int t = blockIdx.x * kWarpsPerBlock + w;
+  if (t >= A.tiles_max || t >= *A.n_tiles) return;
+  const int2 se = A.tiles[t];
+  const int64_t base = (int64_t)(se.x / kTilePts) * kTilePts;
   float2 x[kRowsPerWarp], y[kRowsPerWarp], z[kRowsPerWarp];
   bool va[kRowsPerWarp], vb[kRowsPerWarp];
-  load_points(A, D, tile_base, x, y, z, va, vb);
+  load_points(A, D, base, se.x, se.y, x, y, z, va, vb);
   int s_glob, s_sse;
   fixed_exponents(A.st, A.n, &s_glob, &s_sse);
   int bad = 0;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    const int64_t i = tile_base + r * kRowPts + 2 * lane;
-    if (tile_base + r * kRowPts >= A.n) break;
+    const int64_t i = base + r * kRowPts + 2 * lane;
+    if (!__any_sync(0xffffffffu, va[r] || vb[r])) continue;
     int la = va[r] ? ulab[perm[i]] : 0;
     int lb = vb[r] ? ulab[perm[i + 1]] : 0;
     bool oka = va[r] && la >= 0 && la < A.k, okb = vb[r] && lb >= 0 && lb < A.k;
@@ -596,6 +707,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
 // ---------------------------------------------------------------------------
 // k_finalize: labels back to the caller's order; optional SSE against the
 // current centroids (same FP32 distance expression, fixed-point sum).
+// One warp per 256-window of the sorted order.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kBlockThreads) k_finalize(IterArgs A,
@@ -603,16 +715,16 @@ __global__ void __launch_bounds__(kBlockThreads) k_finalize(IterArgs A,
                                                            int32_t* __restrict__ labels_out,
                                                            int do_sse) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  const int64_t tile_base = tile * kTilePts;
-  if (tile_base >= A.n) return;
+  const int64_t win = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+  const int64_t base = win * kTilePts;
+  if (base >= A.n) return;
   int s_glob, s_sse;
   fixed_exponents(A.st, A.n, &s_glob, &s_sse);
   long long sse = 0;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    const int64_t i = tile_base + r * kRowPts + 2 * lane;
-    if (tile_base + r * kRowPts >= A.n) break;
+    const int64_t i = base + r * kRowPts + 2 * lane;
+    if (base + r * kRowPts >= A.n) break;
     const bool va = i < A.n, vb = i + 1 < A.n;
     const int la = va ? A.lab[i] : 0, lb = vb ? A.lab[i + 1] : 0;
     if (labels_out) {
@@ -636,7 +748,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_finalize(IterArgs A,
       sse += row_sse(d2a, d2b, va, vb, s_sse);
     }
   }
-  if (do_sse && lane == 0) red_add_u64(&A.slots[tile & (kSlots - 1)].sse, (unsigned long long)sse);
+  if (do_sse && lane == 0) red_add_u64(&A.slots[win & (kSlots - 1)].sse, (unsigned long long)sse);
 }
 
 __global__ void k_export(const float4* __restrict__ cw, int k, int d, float* __restrict__ out) {
@@ -666,17 +778,18 @@ cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const fl
 }
 
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
-  k_search<<<ceil_div(A.n_blocks, kSearchWarps), 32 * kSearchWarps, 0, s>>>(A, par, d);
+  k_search<<<ceil_div(A.tiles_max, kSearchWarps), 32 * kSearchWarps, 0, s>>>(A, par, d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s) {
+  const int g = ceil_div(A.tiles_max, kWarpsPerBlock);
   if (d == 3) {
-    if (brute) k_assign<3, true><<<A.n_blocks, kBlockThreads, 0, s>>>(A);
-    else k_assign<3, false><<<A.n_blocks, kBlockThreads, 0, s>>>(A);
+    if (brute) k_assign<3, true><<<g, kBlockThreads, 0, s>>>(A);
+    else k_assign<3, false><<<g, kBlockThreads, 0, s>>>(A);
   } else {
-    if (brute) k_assign<2, true><<<A.n_blocks, kBlockThreads, 0, s>>>(A);
-    else k_assign<2, false><<<A.n_blocks, kBlockThreads, 0, s>>>(A);
+    if (brute) k_assign<2, true><<<g, kBlockThreads, 0, s>>>(A);
+    else k_assign<2, false><<<g, kBlockThreads, 0, s>>>(A);
   }
   return cudaGetLastError();
 }
@@ -688,15 +801,17 @@ cudaError_t launch_collect(const IterArgs& A, int t, cudaStream_t s) {
 
 cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
                                 const uint32_t* perm, cudaStream_t s) {
-  if (d == 3) k_accum_labels<3><<<A.n_blocks, kBlockThreads, 0, s>>>(A, ulab, perm);
-  else k_accum_labels<2><<<A.n_blocks, kBlockThreads, 0, s>>>(A, ulab, perm);
+  const int g = ceil_div(A.tiles_max, kWarpsPerBlock);
+  if (d == 3) k_accum_labels<3><<<g, kBlockThreads, 0, s>>>(A, ulab, perm);
+  else k_accum_labels<2><<<g, kBlockThreads, 0, s>>>(A, ulab, perm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int32_t* labels_out,
                             int do_sse, cudaStream_t s) {
-  if (d == 3) k_finalize<3><<<A.n_blocks, kBlockThreads, 0, s>>>(A, perm, labels_out, do_sse);
-  else k_finalize<2><<<A.n_blocks, kBlockThreads, 0, s>>>(A, perm, labels_out, do_sse);
+  const int g = ceil_div(A.n_windows, kWarpsPerBlock);
+  if (d == 3) k_finalize<3><<<g, kBlockThreads, 0, s>>>(A, perm, labels_out, do_sse);
+  else k_finalize<2><<<g, kBlockThreads, 0, s>>>(A, perm, labels_out, do_sse);
   return cudaGetLastError();
 }
 

@@ -4,15 +4,19 @@
 // iteration (Section IV-A, "Indexes on Spatial Vectors and Centroids";
 // Algorithm 1, first step).  The GPU analog here: sort the points along a
 // Morton (Z-order) curve so that consecutive points are spatially close,
-// cut the sorted order into fixed tiles and blocks, and store one static
-// axis-aligned bounding box per tile and per block.  Points never move, so
-// the boxes stay valid for the whole run.
+// then cut the sorted order into tiles of at most 256 points that never
+// leave one Morton cube of a chosen level (the cube bounds a tile's extent
+// the way a node's radius bounds a ball), and store one static
+// axis-aligned bounding box per tile.  Points never move, so the boxes stay
+// valid for the whole run.
 //
-//   k_bbox       bounding box of the input (+ non-finite / range check)
-//   k_morton     30-bit Morton key per point (3 x 10 or 2 x 15 bits)
-//   k_rs_*       stable LSD radix sort of (key, index), 8-bit digits
-//   k_gather     sorted structure-of-arrays copy of the points
-//   k_boxes      per-tile and per-block AABBs
+//   k_bbox         bounding box of the input (+ non-finite / range check)
+//   k_morton       30-bit Morton key per point (3 x 10 or 2 x 15 bits)
+//   k_rs_*         stable LSD radix sort of (key, index), 8-bit digits
+//   k_gather       sorted structure-of-arrays copy of the points
+//   k_levels       how many Morton cubes each level would cut the order into
+//   k_tiles_*      tiles: 256-point windows split at cube boundaries
+//   k_tile_boxes   per-tile AABBs
 #include "dkm_host.h"
 
 namespace dkm {
@@ -61,7 +65,8 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int64
   }
 }
 
-// reset both boxes to the empty box; 2D contexts pin the z range to [0, 0]
+// reset a box to the empty box (2D contexts pin the z range to [0, 0]) and
+// clear the bad-input flag
 __global__ void k_reset_boxes(DevState* st, int d, int which_mask) {
   int t = threadIdx.x;
   if (t < 3) {
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const uint32_t* __res
   counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of one block-sum per thread across a 256-thread CTA
+// exclusive scan of one value per thread across a 256-thread CTA
 __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t v, uint32_t* s_warp,
                                                             uint32_t* total) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -267,25 +272,122 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ p, int
 }
 
 // ---------------------------------------------------------------------------
-// per-tile and per-block AABBs (one CTA per block, one warp per tile)
+// Tiling.  Level l of the Morton code splits the domain into 2^(d*l) cubes;
+// a cube's points are contiguous in the sorted order.  k_levels counts, for
+// each level, how many sorted neighbours first differ at that level (a cube
+// boundary of that level and every finer one).  The host then picks the
+// finest level whose cube count keeps the extra tiles below 1/8.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlockThreads) k_boxes(const float* __restrict__ xs,
-                                                         const float* __restrict__ ys,
-                                                         const float* __restrict__ zs, int64_t n,
-                                                         int d, float4* __restrict__ tbox,
-                                                         float4* __restrict__ bbox) {
-  __shared__ float4 s_lo[kWarpsPerBlock], s_hi[kWarpsPerBlock];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+__device__ __forceinline__ int first_diff_level(uint32_t a, uint32_t b, int d) {
+  const uint32_t x = a ^ b;
+  if (x == 0) return kMaxLevels;          // same cube at every level
+  const int p = 31 - __clz(x);            // highest differing bit
+  const int L = d == 3 ? 10 : 15;
+  return L - p / d;                        // 1 = the coarsest level
+}
+
+__global__ void __launch_bounds__(256) k_levels(const uint32_t* __restrict__ keys, int64_t n,
+                                                int d, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int h[kMaxLevels + 1];
+  if (threadIdx.x <= kMaxLevels) h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += stride)
+    atomicAdd(&h[first_diff_level(keys[i - 1], keys[i], d)], 1u);
+  __syncthreads();
+  if (threadIdx.x <= kMaxLevels && h[threadIdx.x])
+    atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+// a sorted position starts a tile if it starts a 256-window or a cube
+__device__ __forceinline__ bool tile_starts(const uint32_t* __restrict__ keys, int64_t i,
+                                            int shift) {
+  if ((i & (kTilePts - 1)) == 0) return true;
+  return (keys[i] >> shift) != (keys[i - 1] >> shift);
+}
+
+// one warp per 256-window: number of tiles that start in it
+__global__ void __launch_bounds__(256) k_tiles_count(const uint32_t* __restrict__ keys, int64_t n,
+                                                     int shift, int n_windows,
+                                                     int* __restrict__ wcnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= n_windows) return;
+  int c = 0;
   for (int j = 0; j < kTilePts / 32; ++j) {
-    int64_t i = tile * kTilePts + j * 32 + lane;
-    if (i < n) {
-      float v0 = xs[i], v1 = ys[i], v2 = d == 3 ? zs[i] : 0.f;
-      lo[0] = fminf(lo[0], v0); hi[0] = fmaxf(hi[0], v0);
-      lo[1] = fminf(lo[1], v1); hi[1] = fmaxf(hi[1], v1);
-      lo[2] = fminf(lo[2], v2); hi[2] = fmaxf(hi[2], v2);
-    }
+    const int64_t i = w * kTilePts + j * 32 + lane;
+    c += __popc(__ballot_sync(0xffffffffu, i < n && tile_starts(keys, i, shift)));
+  }
+  if (lane == 0) wcnt[w] = c;
+}
+
+// single CTA: exclusive scan of the per-window tile counts; total -> *n_tiles
+__global__ void __launch_bounds__(1024) k_scan_windows(const int* __restrict__ wcnt, int n_windows,
+                                                       int* __restrict__ wbase,
+                                                       int* __restrict__ n_tiles) {
+  __shared__ int s_part[1024];
+  const int per = (n_windows + 1023) / 1024;
+  const int start = threadIdx.x * per;
+  int sum = 0;
+  for (int i = start; i < start + per && i < n_windows; ++i) sum += wcnt[i];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan
+    int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = s_part[threadIdx.x] - sum;
+  for (int i = start; i < start + per && i < n_windows; ++i) {
+    wbase[i] = run;
+    run += wcnt[i];
+  }
+  if (threadIdx.x == 1023) *n_tiles = s_part[1023];
+}
+
+// one warp per window: write [start, end) of every tile that starts in it
+__global__ void __launch_bounds__(256) k_tiles_write(const uint32_t* __restrict__ keys, int64_t n,
+                                                     int shift, int n_windows,
+                                                     const int* __restrict__ wbase,
+                                                     int2* __restrict__ tiles) {
+  __shared__ int s_pos[8][kTilePts + 1];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * 8 + wl;
+  if (w >= n_windows) return;
+  const unsigned lt = (1u << lane) - 1u;
+  int c = 0;
+  for (int j = 0; j < kTilePts / 32; ++j) {
+    const int64_t i = w * kTilePts + j * 32 + lane;
+    const bool f = i < n && tile_starts(keys, i, shift);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (f) s_pos[wl][c + __popc(bal & lt)] = (int)i;
+    c += __popc(bal);
+  }
+  const int64_t wend = min((int64_t)(w + 1) * kTilePts, n);
+  if (lane == 0) s_pos[wl][c] = (int)wend;
+  __syncwarp();
+  const int base = wbase[w];
+  for (int j = lane; j < c; j += 32) tiles[base + j] = make_int2(s_pos[wl][j], s_pos[wl][j + 1]);
+}
+
+// one warp per tile: AABB of its points
+__global__ void __launch_bounds__(256) k_tile_boxes(const float* __restrict__ xs,
+                                                    const float* __restrict__ ys,
+                                                    const float* __restrict__ zs, int d,
+                                                    const int2* __restrict__ tiles,
+                                                    const int* __restrict__ n_tiles,
+                                                    int tiles_max, float4* __restrict__ tbox) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (t >= tiles_max || t >= *n_tiles) return;
+  const int2 se = tiles[t];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = se.x + lane; i < se.y; i += 32) {
+    float v0 = xs[i], v1 = ys[i], v2 = d == 3 ? zs[i] : 0.f;
+    lo[0] = fminf(lo[0], v0); hi[0] = fmaxf(hi[0], v0);
+    lo[1] = fminf(lo[1], v1); hi[1] = fmaxf(hi[1], v1);
+    lo[2] = fminf(lo[2], v2); hi[2] = fmaxf(hi[2], v2);
   }
   for (int a = 0; a < 3; ++a) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -294,21 +396,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_boxes(const float* __restrict
     }
   }
   if (lane == 0) {
-    float4 l = make_float4(lo[0], lo[1], lo[2], 0.f), h = make_float4(hi[0], hi[1], hi[2], 0.f);
-    tbox[2 * tile] = l;
-    tbox[2 * tile + 1] = h;
-    s_lo[w] = l;
-    s_hi[w] = h;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float4 l = s_lo[0], h = s_hi[0];
-    for (int ww = 1; ww < kWarpsPerBlock; ++ww) {
-      l.x = fminf(l.x, s_lo[ww].x); l.y = fminf(l.y, s_lo[ww].y); l.z = fminf(l.z, s_lo[ww].z);
-      h.x = fmaxf(h.x, s_hi[ww].x); h.y = fmaxf(h.y, s_hi[ww].y); h.z = fmaxf(h.z, s_hi[ww].z);
-    }
-    bbox[2 * blockIdx.x] = l;
-    bbox[2 * blockIdx.x + 1] = h;
+    tbox[2 * t] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    tbox[2 * t + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
   }
 }
 
@@ -359,9 +448,27 @@ cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* orde
   return cudaGetLastError();
 }
 
-cudaError_t launch_boxes(const float* xs, const float* ys, const float* zs, int64_t n, int d,
-                         int n_blocks, float4* tbox, float4* bbox, cudaStream_t s) {
-  k_boxes<<<n_blocks, kBlockThreads, 0, s>>>(xs, ys, zs, n, d, tbox, bbox);
+cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, unsigned long long* hist,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (kMaxLevels + 1), s);
+  if (e != cudaSuccess) return e;
+  k_levels<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(keys, n, d, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tiles(const uint32_t* keys, int64_t n, int shift, int n_windows, int* wcnt,
+                         int* wbase, int* n_tiles, int2* tiles, cudaStream_t s) {
+  const int g = (n_windows + 7) / 8;
+  k_tiles_count<<<g, 256, 0, s>>>(keys, n, shift, n_windows, wcnt);
+  k_scan_windows<<<1, 1024, 0, s>>>(wcnt, n_windows, wbase, n_tiles);
+  k_tiles_write<<<g, 256, 0, s>>>(keys, n, shift, n_windows, wbase, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
+                              const int2* tiles, const int* n_tiles, int tiles_max, float4* tbox,
+                              cudaStream_t s) {
+  k_tile_boxes<<<(tiles_max + 7) / 8, 256, 0, s>>>(xs, ys, zs, d, tiles, n_tiles, tiles_max, tbox);
   return cudaGetLastError();
 }
 

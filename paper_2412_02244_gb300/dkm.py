@@ -52,9 +52,9 @@ class dkm_timings(ctypes.Structure):
 
 
 class dkm_stats(ctypes.Structure):
-    _fields_ = [("evals_per_point", ctypes.c_double), ("candidates_per_block", ctypes.c_double),
-                ("fallback_blocks", ctypes.c_int64), ("grid_overflow", ctypes.c_int64),
-                ("passes", ctypes.c_int)]
+    _fields_ = [("evals_per_point", ctypes.c_double), ("candidates_per_tile", ctypes.c_double),
+                ("fallback_tiles", ctypes.c_int64), ("grid_overflow", ctypes.c_int64),
+                ("tiles", ctypes.c_int64), ("tile_level", ctypes.c_int), ("passes", ctypes.c_int)]
 
 
 _lib: Optional[ctypes.CDLL] = None

@@ -203,7 +203,7 @@ def test_candidate_list_overflow_fallback(dkm, oracle):
     ctx = make_ctx(dkm, pts, k)
     lab, sse, _ = gpu_assign(dkm, ctx, init)
     st = dkm.dkm_last_stats(ctx)
-    assert st.fallback_blocks > 0
+    assert st.fallback_tiles > 0
     lab_o, best, second = oracle.assign(pts, init.astype(np.float64))
     check_labels(lab, lab_o, best, second)
     assert np.array_equal(lab, gpu_assign(dkm, make_ctx(dkm, pts, k, algo=1), init)[0])
