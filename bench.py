@@ -39,7 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = None          # {"sha": ..., "bytes_per_launch": ...}
+NCU_TRAFFIC = {"sha": "0002192177e468ce", "bytes_per_launch": 127_327_744 + 21_182_720,
+               "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
 def kernel_sha() -> str:
@@ -141,9 +142,13 @@ def cpu_sample_run(w, m: int, seed: int = 0):
     threads)."""
     import oracle
     o = oracle.get()
-    rng = np.random.default_rng(seed)
-    idx = rng.choice(w.n, size=m, replace=False)
-    sample = np.ascontiguousarray(w.points[idx])
+    if m >= w.n:
+        m = w.n
+        sample = w.points
+    else:
+        rng = np.random.default_rng(seed)
+        idx = rng.choice(w.n, size=m, replace=False)
+        sample = np.ascontiguousarray(w.points[idx])
     t0 = time.perf_counter()
     o.fit(sample, w.init.astype(np.float64), 1, early_stop=False)
     dt = time.perf_counter() - t0
@@ -332,9 +337,10 @@ def run_ours(args):
     if ws == 1 and not args.no_cpu_baseline:
         v, dt, thr = cpu_sample_run(w, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle",
-                                "sample": f"one FP64 brute-force Lloyd iteration of "
-                                          f"{args.cpu_sample} sampled points against all "
-                                          f"k=10000 centroids ({dt:.1f} s)"}
+                                "sample": f"one FP64 brute-force Lloyd iteration (assignment "
+                                          f"against all k=10000 centroids + update) of "
+                                          f"{min(args.cpu_sample, n)} of the workload's {n} "
+                                          f"points ({dt:.1f} s)"}
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -351,7 +357,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", type=int, default=1,
                     help="record per-kernel CUDA events inside the run graph (roofline)")
-    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-brute", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
