@@ -221,6 +221,42 @@ DKM_API dkm_status dkm_last_stats(dkm_ctx* ctx, dkm_stats* out);
 /* Free the context and its device memory.  NULL is a no-op. */
 DKM_API void dkm_destroy(dkm_ctx* ctx);
 
+/* Largest k dkm_lloyd_step_noalloc accepts (its fixed scratch holds k
+ * cluster accumulators of 32 bytes each, about 2 MiB in all). */
+#define DKM_NOALLOC_MAX_K 65536
+
+/*
+ * One Lloyd step (brute-force assignment of every point, then the update)
+ * that allocates no device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that
+ * runs inside a host framework which owns all device memory through its
+ * own allocator, or a latency-critical loop where cudaMalloc / cudaFree
+ * would synchronise the device.
+ *
+ * points (n x d), centroids (k x d): device pointers, read.
+ * centroids_out (k x d): device pointer, written with the cluster means
+ *   (an empty cluster keeps its centroid); must not alias centroids.
+ * labels (n): device pointer, written, nearest centroid of each point
+ *   (ties to the lowest index), in input order.
+ * sse_out (nullable): host pointer, receives the SSE of the labels against
+ *   the input centroids; the call then waits for the stream.
+ * stream: cudaStream_t (NULL = legacy default stream).
+ *
+ * Scratch: one fixed device array inside the library (per-cluster sums for
+ * up to DKM_NOALLOC_MAX_K clusters, SSE counters, a bounding box).  Every
+ * GPU that loads the library holds it until the process exits.  The first
+ * call on a device looks up that array's device address on the current
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Each call clears what must start at zero.  All calls share the
+ * one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race; serialise them.  Inputs are not checked for NaN/Inf.
+ * Errors: DKM_EINVAL (d not 2/3, n < 1, k < 1 or k > DKM_NOALLOC_MAX_K,
+ * null pointer) before any GPU work; DKM_ECUDA.
+ */
+DKM_API dkm_status dkm_lloyd_step_noalloc(const float* points, int64_t n, int d, int k,
+                                          const float* centroids, float* centroids_out,
+                                          int32_t* labels, double* sse_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -435,6 +435,8 @@ dkm_status validate_sizes(int64_t n, int d, int k) {
 
 }  // namespace
 
+void dkm::dkm_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

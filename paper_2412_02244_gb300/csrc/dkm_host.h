@@ -43,6 +43,9 @@ cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int3
                             int do_sse, cudaStream_t s);
 cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s);
 
+// dkm_api.cu: set the calling thread's dkm_last_error() message
+void dkm_set_last_error(const char* msg);
+
 }  // namespace dkm
 
 struct dkm_ctx {

@@ -89,7 +89,13 @@ _SIGS = [
     ("dkm_last_timings", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dkm_timings)]),
     ("dkm_last_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dkm_stats)]),
     ("dkm_destroy", None, [ctypes.c_void_p]),
+    ("dkm_lloyd_step_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.c_void_p]),
 ]
+
+DKM_NOALLOC_MAX_K = 65536
 
 
 def lib() -> ctypes.CDLL:
@@ -274,3 +280,18 @@ def dkm_last_stats(ctx: Context) -> dkm_stats:
 
 def dkm_destroy(ctx: Context) -> None:
     ctx.close()
+
+
+def dkm_lloyd_step_noalloc(points, n: int, d: int, k: int, centroids, centroids_out, labels,
+                           stream: int = 0) -> float:
+    """One brute-force Lloyd step that allocates no device memory (for
+    callers that cannot call cudaMalloc).  All arrays are device tensors;
+    returns the SSE of the labels against the input centroids."""
+    p, _k0 = _arr(points, "float32", n * d, "points")
+    c, _k1 = _arr(centroids, "float32", k * d, "centroids")
+    co, _k2 = _arr(centroids_out, "float32", k * d, "centroids_out")
+    lab, _k3 = _arr(labels, "int32", n, "labels")
+    sse = ctypes.c_double()
+    _check(lib().dkm_lloyd_step_noalloc(p, n, d, k, c, co, lab, ctypes.byref(sse),
+                                        ctypes.c_void_p(stream or 0)), "dkm_lloyd_step_noalloc")
+    return sse.value

@@ -107,6 +107,14 @@ def test_binding_type_checks(dkm):
         dkm.dkm_create(np.zeros(6, np.float32), 4, 2, 1)
 
 
+def test_noalloc_rejects_k_beyond_its_scratch(dkm):
+    # size checks come before any GPU work, so this runs without a GPU
+    status = dkm.lib().dkm_lloyd_step_noalloc(None, 10, 3, dkm.DKM_NOALLOC_MAX_K + 1, None, None,
+                                              None, None, None)
+    assert status == dkm.DKM_EINVAL
+    assert "DKM_NOALLOC_MAX_K" in dkm.dkm_last_error()
+
+
 def test_create_validates_before_touching_the_gpu(dkm):
     with pytest.raises(dkm.DkmError) as e:
         dkm.dkm_create(np.zeros(8, np.float32), 4, 2, 5)     # k > n
