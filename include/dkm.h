@@ -73,7 +73,7 @@ typedef struct {
      * until it fits, like the paper's memory-tunable leaf capacity.
      * 0 = default (64 MiB). */
     size_t mem_budget_bytes;
-    /* Target grid cells per centroid before the budget cap (default 2.0). */
+    /* Target grid cells per centroid before the budget cap (default 1.0). */
     float cells_per_centroid;
     /* DKM_ALGO_INDEXED (default) or DKM_ALGO_BRUTE. */
     int algo;

@@ -65,7 +65,7 @@ dkm_options resolve(const dkm_options* o) {
   if (o) {
     r = *o;
     if (r.mem_budget_bytes == 0) r.mem_budget_bytes = kDefaultBudget;
-    if (!(r.cells_per_centroid > 0.f)) r.cells_per_centroid = 2.0f;
+    if (!(r.cells_per_centroid > 0.f)) r.cells_per_centroid = 1.0f;
   }
   return r;
 }
@@ -446,7 +446,7 @@ void dkm_default_options(dkm_options* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
   o->mem_budget_bytes = kDefaultBudget;
-  o->cells_per_centroid = 2.0f;
+  o->cells_per_centroid = 1.0f;
   o->algo = DKM_ALGO_INDEXED;
   o->early_stop = 1;
   o->profile = 0;

@@ -163,13 +163,25 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
 // The list is written unordered; k_assign picks the lexicographic minimum
 // of (d^2, id), which does not depend on the order.
 // ---------------------------------------------------------------------------
-constexpr int kSearchWarps = 8;
+constexpr int kSearchWarps = 2;   // independent warps: small CTAs free SM slots early
 
 __device__ __forceinline__ long long cell_index(const Grid& G, int cx, int cy, int cz) {
   return ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
 }
 
-__global__ void __launch_bounds__(32 * kSearchWarps, 3) k_search(IterArgs A, int par, int d) {
+// q-th cell (x fastest) of an nx x ny x nz range; q < 2^31 (the cell paths
+// only run for ranges below the flat-scan threshold), so 32-bit division
+// suffices -- 64-bit division is emulated and far slower.
+__device__ __forceinline__ void decode_cell(long long q, int nx, int ny, int& dx, int& dy, int& dz) {
+  const unsigned uq = (unsigned)q;
+  const unsigned r = uq / (unsigned)nx;
+  dx = (int)(uq - r * (unsigned)nx);
+  const unsigned z = r / (unsigned)ny;
+  dy = (int)(r - z * (unsigned)ny);
+  dz = (int)z;
+}
+
+__global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(IterArgs A, int par, int d) {
   if (A.early_stop && A.st->done) return;
   // clear the other parity's grid for the next rebuild (nobody reads it now)
   {
@@ -223,11 +235,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 3) k_search(IterArgs A, int
     }
     const int nx = rhi[0] - rlo[0] + 1, ny = rhi[1] - rlo[1] + 1;
     for (long long q = lane; q < ncell; q += 32) {
-      int cx = rlo[0] + (int)(q % nx);
-      long long r = q / nx;
-      int cy = rlo[1] + (int)(r % ny);
-      int cz = rlo[2] + (int)(r / ny);
-      long long cell = cell_index(G, cx, cy, cz);
+      int ox, oy, oz;
+      decode_cell(q, nx, ny, ox, oy, oz);
+      long long cell = cell_index(G, rlo[0] + ox, rlo[1] + oy, rlo[2] + oz);
       int cnt = min(gcnt[cell], kBucketCap);
       float4 e[kBucketCap];
 #pragma unroll
@@ -289,11 +299,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 3) k_search(IterArgs A, int
       long long cell = 0;
       int cnt = 0;
       if (q < ncell) {
-        int cx = rlo[0] + (int)(q % nx);
-        long long r = q / nx;
-        int cy = rlo[1] + (int)(r % ny);
-        int cz = rlo[2] + (int)(r / ny);
-        cell = cell_index(G, cx, cy, cz);
+        int ox, oy, oz;
+        decode_cell(q, nx, ny, ox, oy, oz);
+        cell = cell_index(G, rlo[0] + ox, rlo[1] + oy, rlo[2] + oz);
         cnt = min(gcnt[cell], kBucketCap);
       }
       float4 e[kBucketCap];
@@ -336,8 +344,13 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 3) k_search(IterArgs A, int
 // ---------------------------------------------------------------------------
 // k_assign<D, BRUTE>: one warp per tile of 4 rows x 64 points, two points
 // per lane evaluated as packed f32x2.  Warps are independent (no CTA-wide
-// barrier): each stages its own candidate list in shared memory.
+// barrier): each stages its own candidate list in shared memory, so small
+// CTAs free their SM slot as soon as their own tiles are done.
 // ---------------------------------------------------------------------------
+#ifndef DKM_ASSIGN_WARPS
+#define DKM_ASSIGN_WARPS 2
+#endif
+constexpr int kAssignWarps = DKM_ASSIGN_WARPS;
 template <int D>
 struct Pts {
   float2 x[kRowsPerWarp], y[kRowsPerWarp], z[kRowsPerWarp];
@@ -508,6 +521,110 @@ __device__ __forceinline__ void accumulate_row(const IterArgs& A, int D, float2 
   }
 }
 
+// Tile epilogue shared by k_assign and k_accum_labels: residuals p - c of
+// all the tile's points (4 rows x 2 per lane) in 32-bit fixed point with
+// one tile-wide power-of-two scale (256 * max|r| * 2^s < 2^31, so int32
+// sums cannot overflow), grouped by label across the whole tile and added
+// to the per-centroid accumulators with 64-bit integer atomics.  The
+// grouping depends only on the tile and the labels, so every caller gets
+// the same sums bit for bit.
+template <int D>
+__device__ __forceinline__ void accumulate_tile(const IterArgs& A, const float2 (&px)[kRowsPerWarp],
+                                                const float2 (&py)[kRowsPerWarp],
+                                                const float2 (&pz)[kRowsPerWarp],
+                                                const int2 (&lab)[kRowsPerWarp],
+                                                const bool (&va)[kRowsPerWarp],
+                                                const bool (&vb)[kRowsPerWarp], int s_glob) {
+  float rx[2 * kRowsPerWarp], ry[2 * kRowsPerWarp], rz[2 * kRowsPerWarp];
+  float ml = 0.f;
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    rx[2 * r] = ry[2 * r] = rz[2 * r] = 0.f;
+    rx[2 * r + 1] = ry[2 * r + 1] = rz[2 * r + 1] = 0.f;
+    if (va[r]) {
+      const float4 c = __ldg(&A.cw[lab[r].x]);
+      rx[2 * r] = __fadd_rn(px[r].x, -c.x);
+      ry[2 * r] = __fadd_rn(py[r].x, -c.y);
+      if (D == 3) rz[2 * r] = __fadd_rn(pz[r].x, -c.z);
+    }
+    if (vb[r]) {
+      const float4 c = __ldg(&A.cw[lab[r].y]);
+      rx[2 * r + 1] = __fadd_rn(px[r].y, -c.x);
+      ry[2 * r + 1] = __fadd_rn(py[r].y, -c.y);
+      if (D == 3) rz[2 * r + 1] = __fadd_rn(pz[r].y, -c.z);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      ml = fmaxf(ml, fmaxf(fmaxf(fabsf(rx[2 * r + h]), fabsf(ry[2 * r + h])), fabsf(rz[2 * r + h])));
+  }
+  const float m = warp_max_nonneg(ml);
+  const int s_t = m > 0.f ? min(22 - exp_bound(m), 127) : 0;
+  const float sc = pow2f(s_t);
+  int qx[2 * kRowsPerWarp], qy[2 * kRowsPerWarp], qz[2 * kRowsPerWarp], lb[2 * kRowsPerWarp];
+  bool pend[2 * kRowsPerWarp];
+#pragma unroll
+  for (int h = 0; h < 2 * kRowsPerWarp; ++h) {
+    qx[h] = __float2int_rn(rx[h] * sc);
+    qy[h] = __float2int_rn(ry[h] * sc);
+    qz[h] = D == 3 ? __float2int_rn(rz[h] * sc) : 0;
+    lb[h] = (h & 1) ? lab[h >> 1].y : lab[h >> 1].x;
+    pend[h] = (h & 1) ? vb[h >> 1] : va[h >> 1];
+  }
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    // label of the first pending point (slot-major, then lane)
+    int L = -1;
+#pragma unroll
+    for (int h = 0; h < 2 * kRowsPerWarp; ++h) {
+      const unsigned mk = __ballot_sync(0xffffffffu, pend[h]);
+      if (L < 0 && mk) L = __shfl_sync(0xffffffffu, lb[h], __ffs(mk) - 1);
+    }
+    if (L < 0) break;
+    int sx = 0, sy = 0, sz = 0, cnt = 0;
+#pragma unroll
+    for (int h = 0; h < 2 * kRowsPerWarp; ++h) {
+      const bool g = pend[h] && lb[h] == L;
+      sx += g ? qx[h] : 0;
+      sy += g ? qy[h] : 0;
+      sz += g ? qz[h] : 0;
+      cnt += g ? 1 : 0;
+      pend[h] = pend[h] && !g;
+    }
+    sx = __reduce_add_sync(0xffffffffu, sx);
+    sy = __reduce_add_sync(0xffffffffu, sy);
+    if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0) {
+      Acc* a = &A.acc[L];
+      red_add_u64(&a->s[0], (unsigned long long)rescale(sx, s_t, s_glob));
+      red_add_u64(&a->s[1], (unsigned long long)rescale(sy, s_t, s_glob));
+      if (D == 3) red_add_u64(&a->s[2], (unsigned long long)rescale(sz, s_t, s_glob));
+      red_add_u64(&a->cnt, (unsigned long long)cnt);
+    }
+  }
+}
+
+// Tile SSE in fixed point (unit 2^-s_sse) with one tile-wide scale
+// (256 * max d^2 * 2^s < 2^31), identical on every lane.
+__device__ __forceinline__ long long tile_sse(const float2 (&best)[kRowsPerWarp],
+                                             const bool (&va)[kRowsPerWarp],
+                                             const bool (&vb)[kRowsPerWarp], int s_sse) {
+  float ml = 0.f;
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r)
+    ml = fmaxf(ml, fmaxf(va[r] ? best[r].x : 0.f, vb[r] ? best[r].y : 0.f));
+  const float m = warp_max_nonneg(ml);
+  const int s2 = m > 0.f ? min(22 - exp_bound(m), 127) : 0;
+  const float sc = pow2f(s2);
+  unsigned q = 0;
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    q += va[r] ? (unsigned)__float2uint_rn(best[r].x * sc) : 0u;
+    q += vb[r] ? (unsigned)__float2uint_rn(best[r].y * sc) : 0u;
+  }
+  return rescale((long long)__reduce_add_sync(0xffffffffu, q), s2, s_sse);
+}
+
 // per-row SSE in fixed point (unit 2^-s_sse), identical on every lane
 __device__ __forceinline__ long long row_sse(float d2a, float d2b, bool va, bool vb, int s_sse) {
   float a = va ? d2a : 0.f, b = vb ? d2b : 0.f;
@@ -538,12 +655,13 @@ __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t ba
 }
 
 template <int D, bool BRUTE>
-__global__ void __launch_bounds__(kBlockThreads, 3) k_assign(IterArgs A) {
-  __shared__ float4 s_c[kWarpsPerBlock][kTileCap];
-  __shared__ unsigned short s_r[kWarpsPerBlock][kTileCap];
+__global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2) k_assign(IterArgs A) {
+  __shared__ float4 s_c[kAssignWarps][kTileCap];
+  __shared__ unsigned short s_r[kAssignWarps][kTileCap];
+  __shared__ float slb[kAssignWarps][32];
   if (A.early_stop && A.st->done) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int t = blockIdx.x * kWarpsPerBlock + w;
+  const int t = blockIdx.x * kAssignWarps + w;
   if (t == 0 && lane == 0) atomicAdd(&A.st->passes, 1);
   if (t >= A.tiles_max || t >= *A.n_tiles) return;   // warp-level exit, no CTA barrier below
   const int2 se = A.tiles[t];
@@ -579,11 +697,44 @@ __global__ void __launch_bounds__(kBlockThreads, 3) k_assign(IterArgs A) {
     evals = (unsigned long long)A.k * nv_tile;
   } else {
     const int q = A.tcnt[t];
-    if (q <= kTileCap) {
+    if (q <= 32) {
+      // Short list: order it by the lower bound mind^2(tile box, c) and stop
+      // once the next bound exceeds every point's current best (the kNN
+      // pruning rule of Algorithm 1's kNN function, with the tile box as
+      // the query node).  (d^2, id) keys make the result order independent.
+      if (q == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
+      const float4 tlo = A.tbox[2 * t], thi = A.tbox[2 * t + 1];
+      const bool has = lane < q;
+      const float4 c = has ? __ldg(&A.cw[A.tlist[(int64_t)t * kTileCap + lane]])
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float lb = has ? mind2(tlo, thi, c.x, c.y, c.z, D) : INFINITY;
+      const unsigned long long key =
+          ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)lane;
+      int rank = 0;
+      for (int m = 0; m < q; ++m) rank += __shfl_sync(0xffffffffu, key, m) < key;
+      if (has) {
+        sc[rank] = c;
+        slb[w][rank] = lb;
+      }
+      __syncwarp();
+      int done = 0;
+      for (int j0 = 0; j0 < q; j0 += 4) {
+        if (j0 > 0) {
+          float mb = 0.f;
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            mb = fmaxf(mb, fmaxf(va[r] ? best[r].x : 0.f, vb[r] ? best[r].y : 0.f));
+          if (slb[w][j0] > warp_max_nonneg(mb) * kKeep) break;
+        }
+        const int m = min(4, q - j0);
+        eval_list<D>(sc + j0, nullptr, m, P, best, bid);
+        done = j0 + m;
+      }
+      evals = (unsigned long long)done * nv_tile;
+    } else if (q <= kTileCap) {
       const int* src = A.tlist + (int64_t)t * kTileCap;
       for (int i = lane; i < q; i += 32) sc[i] = __ldg(&A.cw[src[i]]);
       __syncwarp();
-      if (q == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
       if (q > A.row_filter_min) {
         // long list: narrow it again per row of 64 points
 #pragma unroll
@@ -659,9 +810,9 @@ __global__ void __launch_bounds__(kBlockThreads, 3) k_assign(IterArgs A) {
     } else if (vb[r]) {
       A.lab[i + 1] = lb;
     }
-    sse += row_sse(best[r].x, best[r].y, va[r], vb[r], s_sse);
-    accumulate_row(A, D, P.x[r], P.y[r], P.z[r], la, lb, va[r], vb[r], s_glob);
   }
+  sse = tile_sse(best, va, vb, s_sse);
+  accumulate_tile<D>(A, P.x, P.y, P.z, bid, va, vb, s_glob);
   changed = __reduce_add_sync(0xffffffffu, changed);
   if (lane == 0) {
     Slot& s = A.slots[t & (kSlots - 1)];
@@ -691,16 +842,19 @@ __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
   int s_glob, s_sse;
   fixed_exponents(A.st, A.n, &s_glob, &s_sse);
   int bad = 0;
+  int2 lab[kRowsPerWarp];
+  bool oka[kRowsPerWarp], okb[kRowsPerWarp];
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
     const int64_t i = base + r * kRowPts + 2 * lane;
-    if (!__any_sync(0xffffffffu, va[r] || vb[r])) continue;
-    int la = va[r] ? ulab[perm[i]] : 0;
-    int lb = vb[r] ? ulab[perm[i + 1]] : 0;
-    bool oka = va[r] && la >= 0 && la < A.k, okb = vb[r] && lb >= 0 && lb < A.k;
-    bad |= (va[r] && !oka) || (vb[r] && !okb);
-    accumulate_row(A, D, x[r], y[r], z[r], oka ? la : 0, okb ? lb : 0, oka, okb, s_glob);
+    const int la = va[r] ? ulab[perm[i]] : 0;
+    const int lb = vb[r] ? ulab[perm[i + 1]] : 0;
+    oka[r] = va[r] && la >= 0 && la < A.k;
+    okb[r] = vb[r] && lb >= 0 && lb < A.k;
+    bad |= (va[r] && !oka[r]) || (vb[r] && !okb[r]);
+    lab[r] = make_int2(oka[r] ? la : 0, okb[r] ? lb : 0);
   }
+  accumulate_tile<D>(A, x, y, z, lab, oka, okb, s_glob);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&A.st->label_err, 1);
 }
 
@@ -783,13 +937,14 @@ cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
 }
 
 cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s) {
-  const int g = ceil_div(A.tiles_max, kWarpsPerBlock);
+  const int g = ceil_div(A.tiles_max, kAssignWarps);
+  constexpr int thr = 32 * kAssignWarps;
   if (d == 3) {
-    if (brute) k_assign<3, true><<<g, kBlockThreads, 0, s>>>(A);
-    else k_assign<3, false><<<g, kBlockThreads, 0, s>>>(A);
+    if (brute) k_assign<3, true><<<g, thr, 0, s>>>(A);
+    else k_assign<3, false><<<g, thr, 0, s>>>(A);
   } else {
-    if (brute) k_assign<2, true><<<g, kBlockThreads, 0, s>>>(A);
-    else k_assign<2, false><<<g, kBlockThreads, 0, s>>>(A);
+    if (brute) k_assign<2, true><<<g, thr, 0, s>>>(A);
+    else k_assign<2, false><<<g, thr, 0, s>>>(A);
   }
   return cudaGetLastError();
 }

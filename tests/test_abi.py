@@ -46,7 +46,7 @@ def test_binding_names_match_header(dkm):
 def test_default_options(dkm):
     o = dkm.dkm_default_options()
     assert o.mem_budget_bytes == 64 << 20
-    assert o.cells_per_centroid == pytest.approx(2.0)
+    assert o.cells_per_centroid == pytest.approx(1.0)
     assert o.algo == dkm.DKM_ALGO_INDEXED and o.early_stop == 1 and o.profile == 0
     assert dkm.dkm_status_string(1) == "DKM_EINVAL"
 
@@ -72,7 +72,7 @@ def test_plan_respects_budget(dkm, budget_mb):
     p = dkm.dkm_plan(10_000_000, 3, k, [-100, -100, 0], [100, 100, 10], o)
     assert p.index_bytes <= o.mem_budget_bytes
     assert p.cells == p.dims[0] * p.dims[1] * p.dims[2]
-    assert p.cells <= math.ceil(2.0 * k)
+    assert p.cells <= math.ceil(o.cells_per_centroid * k)
     # the grid covers the box: dims * cell >= extent on every axis
     for a, ext in enumerate([200, 200, 10]):
         assert p.dims[a] * p.cell >= ext * (1 - 1e-6)
