@@ -221,6 +221,50 @@ DKM_API dkm_status dkm_last_stats(dkm_ctx* ctx, dkm_stats* out);
 /* Free the context and its device memory.  NULL is a no-op. */
 DKM_API void dkm_destroy(dkm_ctx* ctx);
 
+/*
+ * Differentiable losses of a batch of B point clouds (the differentiable
+ * extension of Eq. 1).  Cloud b holds points[offsets[b] .. offsets[b+1])
+ * (rows of the n_total x d array points); every cloud has k centroids
+ * (1 <= k <= 1024), stored cloud after cloud as B x k x d arrays.
+ * points, init_centroids, ckpt and the gradient arrays are device
+ * pointers; offsets (B + 1, offsets[0] = 0, every cloud non-empty), tau (B),
+ * loss (B) and dloss (B) may be host or device pointers.  Work runs on
+ * stream (a cudaStream_t; NULL = legacy default stream); each call returns
+ * after its outputs are written.  Scratch comes from the stream-ordered
+ * allocator (cudaMallocAsync) and is released before returning.
+ *
+ * Soft k-means with T unrolled steps at a fixed temperature tau[b]:
+ *   w^t_ij = softmax_j(-||p_i - c^t_j||^2 / tau),
+ *   c^{t+1}_j = sum_i w^t_ij p_i / sum_i w^t_ij   (a centroid whose weights
+ *     all underflow to zero in FP32 keeps its position),
+ *   loss[b] = sum_ij w^T_ij ||p_i - c^T_j||^2.
+ * dkm_soft_forward writes the centroids of every step into ckpt
+ * (B x (T+1) x k x d, step-major: ckpt[t] is B x k x d) and the loss.
+ * dkm_soft_backward takes those checkpoints and the upstream gradient
+ * dloss[b] = dOut/dloss[b] and writes dOut/dpoints (n_total x d) and
+ * dOut/dinit_centroids (B x k x d), recomputing the weights of each step
+ * from ckpt instead of storing them.  tau is a constant of the loss.
+ * Errors: DKM_EINVAL (sizes, offsets, null pointers), DKM_ECUDA.
+ */
+DKM_API dkm_status dkm_soft_forward(const float* points, const int64_t* offsets, int B, int d,
+                                    int k, const float* init_centroids, int T, const float* tau,
+                                    float* ckpt, double* loss, void* stream);
+DKM_API dkm_status dkm_soft_backward(const float* points, const int64_t* offsets, int B, int d,
+                                     int k, const float* ckpt, int T, const float* tau,
+                                     const double* dloss, float* grad_points, float* grad_init,
+                                     void* stream);
+
+/*
+ * Hard SSE of each cloud, Eq. 1 with the nearest centroid (lowest index on
+ * ties): loss[b] = sum_i min_j ||p_i - c_j||^2, with optional labels (n_total,
+ * cloud-local centroid index), dloss/dpoints = 2 (p_i - c_a(i)) and
+ * dloss/dcentroids_j = -2 sum_{a(i)=j} (p_i - c_j).  Same layout and pointer
+ * rules as dkm_soft_forward; labels, loss and both gradients may be NULL.
+ */
+DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int B, int d, int k,
+                                const float* centroids, int32_t* labels, double* loss,
+                                float* grad_points, float* grad_centroids, void* stream);
+
 /* Largest k dkm_lloyd_step_noalloc accepts (its fixed scratch holds k
  * cluster accumulators of 32 bytes each, about 2 MiB in all). */
 #define DKM_NOALLOC_MAX_K 65536

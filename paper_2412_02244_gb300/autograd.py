@@ -1,0 +1,86 @@
+"""torch.autograd.Function wrappers of the differentiable k-means losses.
+
+Both run entirely in libdkm's kernels (dkm_soft_forward / dkm_soft_backward
+/ dkm_hard_sse); this module only allocates the output tensors and routes
+the upstream gradient.
+
+  SoftKMeansLoss.apply(points, init, offsets, tau, T) -> loss (B,) float64
+      points  (n_total, d) float32 CUDA, clouds concatenated
+      init    (B, k, d)    float32 CUDA, initial centroids
+      offsets (B + 1,)     int64 (CPU), cloud b = points[offsets[b]:offsets[b+1]]
+      tau     (B,)         float32 (CPU), temperature per cloud (a constant)
+      T       int          unrolled soft k-means steps
+    Gradients flow to points and init.
+
+  HardSSELoss.apply(points, centroids, offsets) -> loss (B,) float64
+    Gradients flow to points and centroids.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import dkm
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def temperature(points: torch.Tensor, offsets: torch.Tensor, frac: float = 0.01) -> torch.Tensor:
+    """tau_b = frac x squared bounding-box diagonal of cloud b (CPU float32)."""
+    out = []
+    off = offsets.tolist()
+    for b in range(len(off) - 1):
+        P = points[off[b]:off[b + 1]]
+        ext = P.max(dim=0).values - P.min(dim=0).values
+        out.append(frac * float((ext.double() ** 2).sum()))
+    return torch.tensor(out, dtype=torch.float32)
+
+
+class SoftKMeansLoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, points, init, offsets, tau, T: int):
+        B, k, d = init.shape
+        points = points.contiguous()
+        init = init.contiguous()
+        offsets = offsets.to(torch.int64).cpu().contiguous()
+        tau = tau.to(torch.float32).cpu().contiguous()
+        ckpt = torch.empty((T + 1, B, k, d), dtype=torch.float32, device=points.device)
+        loss = torch.empty(B, dtype=torch.float64, device=points.device)
+        dkm.dkm_soft_forward(points, offsets, B, d, k, init, T, tau, ckpt, loss, _stream())
+        ctx.save_for_backward(points, ckpt)
+        ctx.meta = (offsets, tau, int(T), B, k, d)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gloss):
+        points, ckpt = ctx.saved_tensors
+        offsets, tau, T, B, k, d = ctx.meta
+        gp = torch.empty_like(points)
+        gi = torch.empty((B, k, d), dtype=torch.float32, device=points.device)
+        dl = gloss.detach().to(torch.float64).contiguous()
+        dkm.dkm_soft_backward(points, offsets, B, d, k, ckpt, T, tau, dl, gp, gi, _stream())
+        return gp, gi, None, None, None
+
+
+class HardSSELoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, points, centroids, offsets):
+        B, k, d = centroids.shape
+        points = points.contiguous()
+        centroids = centroids.contiguous()
+        offsets = offsets.to(torch.int64).cpu().contiguous()
+        loss = torch.empty(B, dtype=torch.float64, device=points.device)
+        gp = torch.empty_like(points)
+        gc = torch.empty_like(centroids)
+        dkm.dkm_hard_sse(points, offsets, B, d, k, centroids, None, loss, gp, gc, _stream())
+        ctx.save_for_backward(gp, gc)
+        ctx.offsets = offsets
+        return loss
+
+    @staticmethod
+    def backward(ctx, gloss):
+        gp, gc = ctx.saved_tensors
+        sizes = (ctx.offsets[1:] - ctx.offsets[:-1]).to(gp.device)
+        w = gloss.to(torch.float32)
+        return gp * torch.repeat_interleave(w, sizes)[:, None], gc * w[:, None, None], None

@@ -1,0 +1,588 @@
+// dkm_soft.cu -- differentiable k-means losses of a batch of point clouds
+// (sm_103a).
+//
+// The paper optimises the k-means objective of Eq. 1 with Lloyd's
+// algorithm.  The differentiable extension exposes two losses and their
+// gradients with respect to the points and the initial centroids:
+//
+//   hard SSE   L_h = sum_i min_j ||p_i - c_j||^2; dL/dp_i = 2 (p_i - c_a(i)),
+//              dL/dc_j = -2 sum_{a(i)=j} (p_i - c_j)
+//   soft       T unrolled soft k-means steps at a fixed temperature tau:
+//              w^t_ij = softmax_j(-||p_i - c^t_j||^2 / tau),
+//              c^{t+1}_j = sum_i w^t_ij p_i / sum_i w^t_ij,
+//              L_s = sum_ij w^T_ij ||p_i - c^T_j||^2.
+//
+// Every (point, centroid) quantity is recomputed, never stored: row passes
+// (one thread per point, reducing over the cloud's centroids in shared
+// memory) and column passes (one thread per centroid, reducing over a split
+// of the cloud's points staged in shared memory).  The backward recomputes
+// the weights of step t from the checkpointed centroids c^t.  Column sums
+// run in FP32 over chunks of 64 points and in FP64 across chunks; splits
+// are combined in a fixed order, so results are deterministic.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dkm_host.h"
+
+namespace dkm {
+namespace {
+
+constexpr int kRowThreads = 256;
+constexpr int kSplit = 2048;       // points per column-pass CTA
+constexpr int kColChunk = 256;     // points staged in shared memory per round
+constexpr int kSubChunk = 64;      // FP32 accumulation run before the FP64 add
+
+struct SoftArgs {
+  const float* P;         // n_total x D, row-major
+  const int64_t* off;     // B + 1 cloud offsets
+  int B, k, ns;           // clouds, centroids per cloud, splits per cloud
+  const float* tau;       // B
+  float* m;               // per point: min_j D_ij
+  float* iz;              // per point: 1 / sum_j exp((m - D_ij) / tau)
+  float* aux;             // per point: rho_i (soft step) or E_i (loss stage)
+  double* part;           // B x ns x k x 4 column partials
+};
+
+enum RowMode { kRowStats = 0, kRowLoss = 1, kRowStep = 2, kRowLossBwd = 3, kRowHard = 4 };
+enum ColMode { kColMean = 0, kColStep = 1, kColLoss = 2, kColHard = 3 };
+
+template <int D>
+__device__ __forceinline__ float3 load_pt(const float* P, int64_t i) {
+  return make_float3(P[i * D + 0], P[i * D + 1], D == 3 ? P[i * D + 2] : 0.f);
+}
+
+template <int D>
+__device__ __forceinline__ float sqd(float3 p, float4 c, float3& diff) {
+  diff.x = __fadd_rn(p.x, -c.x);
+  diff.y = __fadd_rn(p.y, -c.y);
+  diff.z = D == 3 ? __fadd_rn(p.z, -c.z) : 0.f;
+  float s = __fmaf_rn(diff.y, diff.y, __fmul_rn(diff.x, diff.x));
+  if (D == 3) s = __fmaf_rn(diff.z, diff.z, s);
+  return s;
+}
+
+template <int D>
+__device__ __forceinline__ float4 load_c(const float* C, int64_t j, float w) {
+  return make_float4(C[j * D + 0], C[j * D + 1], D == 3 ? C[j * D + 2] : 0.f, w);
+}
+
+// Row pass.  Shared memory: c^t (k), and for kRowStep c^{t+1} with .w = 1/N
+// (k) and the upstream gradient of c^{t+1} (k).
+template <int D, int MODE>
+__global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const float* __restrict__ Ct,
+                                                          const float* __restrict__ Cn,
+                                                          const float* __restrict__ Nn,
+                                                          const float* __restrict__ Gn,
+                                                          const double* __restrict__ dloss,
+                                                          float* __restrict__ gP,
+                                                          int32_t* __restrict__ labels,
+                                                          double* __restrict__ loss_part) {
+  extern __shared__ float4 sm[];
+  __shared__ double s_red[kRowThreads / 32];
+  const int b = blockIdx.y, k = A.k;
+  const int64_t o0 = A.off[b], o1 = A.off[b + 1];
+  float4* sc = sm;
+  float4* scn = sm + k;
+  float4* sg = sm + 2 * k;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const int64_t g = (int64_t)b * k + j;
+    sc[j] = load_c<D>(Ct, g, 0.f);
+    if (MODE == kRowStep) {
+      const float n = Nn[g];
+      scn[j] = load_c<D>(Cn, g, n > 0.f ? 1.f / n : 0.f);
+      sg[j] = load_c<D>(Gn, g, 0.f);
+    }
+  }
+  __syncthreads();
+  const int64_t i = o0 + (int64_t)blockIdx.x * kRowThreads + threadIdx.x;
+  const bool valid = i < o1;
+  const float3 p = valid ? load_pt<D>(A.P, i) : make_float3(0.f, 0.f, 0.f);
+  const float it = 1.f / A.tau[b];
+  double contrib = 0.0;
+  float3 dv;
+  if (MODE == kRowHard) {
+    float best = INFINITY;
+    int a = 0;
+    for (int j = 0; j < k; ++j) {
+      const float s = sqd<D>(p, sc[j], dv);
+      if (s < best) {
+        best = s;
+        a = j;
+      }
+    }
+    if (valid) {
+      labels[i] = a;
+      contrib = best;
+      if (gP) {
+        sqd<D>(p, sc[a], dv);
+        gP[i * D + 0] = 2.f * dv.x;
+        gP[i * D + 1] = 2.f * dv.y;
+        if (D == 3) gP[i * D + 2] = 2.f * dv.z;
+      }
+    }
+  } else {
+    float m = INFINITY;
+    for (int j = 0; j < k; ++j) m = fminf(m, sqd<D>(p, sc[j], dv));
+    float z = 0.f;
+    for (int j = 0; j < k; ++j) z += expf((m - sqd<D>(p, sc[j], dv)) * it);
+    const float iz = 1.f / z;
+    if (MODE == kRowLoss || MODE == kRowLossBwd) {
+      // E = sum_j w D;  B = sum_j w (p - c);  F = sum_j w D (p - c)
+      float E = 0.f;
+      float3 Bv = make_float3(0.f, 0.f, 0.f), F = make_float3(0.f, 0.f, 0.f);
+      for (int j = 0; j < k; ++j) {
+        const float s = sqd<D>(p, sc[j], dv);
+        const float w = expf((m - s) * it) * iz;
+        E = __fmaf_rn(w, s, E);
+        if (MODE == kRowLossBwd) {
+          Bv.x = __fmaf_rn(w, dv.x, Bv.x); Bv.y = __fmaf_rn(w, dv.y, Bv.y); Bv.z = __fmaf_rn(w, dv.z, Bv.z);
+          const float ws = w * s;
+          F.x = __fmaf_rn(ws, dv.x, F.x); F.y = __fmaf_rn(ws, dv.y, F.y); F.z = __fmaf_rn(ws, dv.z, F.z);
+        }
+      }
+      if (valid) {
+        contrib = E;
+        if (MODE == kRowLossBwd) {
+          // dL/dp_i = 2 sum_l w_il (1 - (D_il - E_i)/tau) (p_i - c_l)
+          const float sc2 = 2.f * (float)dloss[b];
+          gP[i * D + 0] = sc2 * (Bv.x - it * (F.x - E * Bv.x));
+          gP[i * D + 1] = sc2 * (Bv.y - it * (F.y - E * Bv.y));
+          if (D == 3) gP[i * D + 2] = sc2 * (Bv.z - it * (F.z - E * Bv.z));
+          A.aux[i] = E;
+        }
+      }
+    } else if (MODE == kRowStep) {
+      // rho = sum_j w g;  Av = sum_j w g (p - c^t);  Bv = sum_j w (p - c^t);
+      // Dir = sum_j w gbar_j / N_j,  g_ij = gbar_j . (p_i - c^{t+1}_j) / N_j
+      float rho = 0.f;
+      float3 Av = make_float3(0.f, 0.f, 0.f), Bv = Av, Dir = Av;
+      for (int j = 0; j < k; ++j) {
+        const float s = sqd<D>(p, sc[j], dv);
+        const float w = expf((m - s) * it) * iz;
+        const float4 cn = scn[j], gb = sg[j];
+        float3 dn;
+        sqd<D>(p, cn, dn);
+        float g = __fmul_rn(gb.x, dn.x);
+        g = __fmaf_rn(gb.y, dn.y, g);
+        if (D == 3) g = __fmaf_rn(gb.z, dn.z, g);
+        g *= cn.w;
+        const float wg = w * g;
+        rho += wg;
+        Av.x = __fmaf_rn(wg, dv.x, Av.x); Av.y = __fmaf_rn(wg, dv.y, Av.y); Av.z = __fmaf_rn(wg, dv.z, Av.z);
+        Bv.x = __fmaf_rn(w, dv.x, Bv.x); Bv.y = __fmaf_rn(w, dv.y, Bv.y); Bv.z = __fmaf_rn(w, dv.z, Bv.z);
+        const float wn = w * cn.w;
+        Dir.x = __fmaf_rn(wn, gb.x, Dir.x); Dir.y = __fmaf_rn(wn, gb.y, Dir.y); Dir.z = __fmaf_rn(wn, gb.z, Dir.z);
+      }
+      if (valid) {
+        // dL/dp_i += Dir + sum_j dD_ij 2 (p_i - c_j),  dD_ij = -(1/tau) w (g - rho)
+        const float two_it = 2.f * it;
+        gP[i * D + 0] += Dir.x - two_it * (Av.x - rho * Bv.x);
+        gP[i * D + 1] += Dir.y - two_it * (Av.y - rho * Bv.y);
+        if (D == 3) gP[i * D + 2] += Dir.z - two_it * (Av.z - rho * Bv.z);
+        A.aux[i] = rho;
+      }
+    }
+    if (valid) {
+      A.m[i] = m;
+      A.iz[i] = iz;
+    }
+  }
+  if (MODE == kRowLoss || MODE == kRowHard) {
+    // deterministic per-CTA partial of the loss
+    double v = contrib;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kRowThreads / 32; ++w) t += s_red[w];
+      loss_part[(int64_t)b * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// Column pass: one thread per centroid j of cloud blockIdx.y, over the
+// points of split blockIdx.x.  Writes part[b][s][j][0..3].
+template <int D, int MODE>
+__global__ void k_soft_col(SoftArgs A, const float* __restrict__ Ct, const float* __restrict__ Cn,
+                           const float* __restrict__ Nn, const float* __restrict__ Gn,
+                           const double* __restrict__ dloss, const int32_t* __restrict__ labels) {
+  __shared__ float4 s_p[kColChunk];   // x, y, z, m
+  __shared__ float4 s_q[kColChunk];   // iz, aux, label bits, -
+  const int b = blockIdx.y, s = blockIdx.x, k = A.k, j = threadIdx.x;
+  const int64_t o0 = A.off[b], o1 = A.off[b + 1];
+  const int64_t lo = o0 + (int64_t)s * kSplit, hi = min(lo + kSplit, o1);
+  const bool live = j < k;
+  const int64_t g = (int64_t)b * k + (live ? j : 0);
+  const float4 c = load_c<D>(Ct, g, 0.f);
+  float4 cn = c, gb = c;
+  float in = 0.f;
+  if (MODE == kColStep) {
+    cn = load_c<D>(Cn, g, 0.f);
+    gb = load_c<D>(Gn, g, 0.f);
+    const float n = Nn[g];
+    in = n > 0.f ? 1.f / n : 0.f;
+  }
+  const float it = 1.f / A.tau[b];
+  const float scl = MODE == kColLoss ? (float)dloss[b] : 1.f;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t c0 = lo; c0 < hi; c0 += kColChunk) {
+    const int m = (int)min((int64_t)kColChunk, hi - c0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+      const float3 p = load_pt<D>(A.P, c0 + q);
+      if (MODE == kColHard) {
+        s_p[q] = make_float4(p.x, p.y, p.z, 0.f);
+        s_q[q] = make_float4(0.f, 0.f, __int_as_float(labels[c0 + q]), 0.f);
+      } else {
+        s_p[q] = make_float4(p.x, p.y, p.z, A.m[c0 + q]);
+        s_q[q] = make_float4(A.iz[c0 + q], MODE == kColMean ? 0.f : A.aux[c0 + q], 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int q0 = 0; q0 < m; q0 += kSubChunk) {
+      float f[4] = {0.f, 0.f, 0.f, 0.f};
+      const int qe = min(q0 + kSubChunk, m);
+      for (int q = q0; q < qe; ++q) {
+        const float4 pq = s_p[q], aq = s_q[q];
+        const float3 p = make_float3(pq.x, pq.y, pq.z);
+        float3 dv;
+        if (MODE == kColHard) {
+          if (__float_as_int(aq.z) == j) {
+            sqd<D>(p, c, dv);
+            f[0] += dv.x; f[1] += dv.y; f[2] += dv.z;
+          }
+          continue;
+        }
+        const float sd = sqd<D>(p, c, dv);
+        const float w = expf((pq.w - sd) * it) * aq.x;
+        if (MODE == kColMean) {
+          f[0] = __fmaf_rn(w, p.x, f[0]);
+          f[1] = __fmaf_rn(w, p.y, f[1]);
+          f[2] = __fmaf_rn(w, p.z, f[2]);
+          f[3] += w;
+        } else if (MODE == kColStep) {
+          float3 dn;
+          sqd<D>(p, cn, dn);
+          float gg = __fmul_rn(gb.x, dn.x);
+          gg = __fmaf_rn(gb.y, dn.y, gg);
+          if (D == 3) gg = __fmaf_rn(gb.z, dn.z, gg);
+          const float dd = -it * w * (gg * in - aq.y);   // dL/dD_ij
+          f[0] = __fmaf_rn(dd, dv.x, f[0]);
+          f[1] = __fmaf_rn(dd, dv.y, f[1]);
+          f[2] = __fmaf_rn(dd, dv.z, f[2]);
+        } else {   // kColLoss: dL/dD_ij = w (1 - (D_ij - E_i) / tau)
+          const float dd = scl * w * (1.f - (sd - aq.y) * it);
+          f[0] = __fmaf_rn(dd, dv.x, f[0]);
+          f[1] = __fmaf_rn(dd, dv.y, f[1]);
+          f[2] = __fmaf_rn(dd, dv.z, f[2]);
+        }
+      }
+      for (int a = 0; a < 4; ++a) acc[a] += (double)f[a];
+    }
+  }
+  if (live) {
+    double* out = A.part + (((int64_t)b * A.ns + s) * k + j) * 4;
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+    out[3] = acc[3];
+  }
+}
+
+// Combine the splits in order.  mean: c_next = S / N (or c if N == 0),
+// N_out = N.  grad: G_out = -2 * sum (the dL/dc of the pass).
+__global__ void k_soft_reduce(SoftArgs A, int D, int mode, const float* __restrict__ Ct,
+                              float* __restrict__ Cnext, float* __restrict__ Nout,
+                              float* __restrict__ Gout) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)A.B * A.k) return;
+  const int b = (int)(idx / A.k), j = (int)(idx % A.k);
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int s = 0; s < A.ns; ++s) {
+    const double* in = A.part + (((int64_t)b * A.ns + s) * A.k + j) * 4;
+    for (int a = 0; a < 4; ++a) t[a] += in[a];
+  }
+  if (mode == 0) {
+    if (Nout) Nout[idx] = (float)t[3];
+    if (Cnext)
+      for (int a = 0; a < D; ++a)
+        Cnext[idx * D + a] = t[3] > 0.0 ? (float)(t[a] / t[3]) : Ct[idx * D + a];
+  } else {
+    for (int a = 0; a < D; ++a) Gout[idx * D + a] = (float)(-2.0 * t[a]);
+  }
+}
+
+__global__ void k_soft_loss(const double* __restrict__ part, int gx, int B, double* __restrict__ loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double t = 0.0;
+  for (int q = 0; q < gx; ++q) t += part[(int64_t)b * gx + q];
+  loss[b] = t;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct SoftPlan {
+  std::vector<int64_t> off;
+  int64_t n_total = 0, max_n = 0;
+  int gx = 0, ns = 0;
+};
+
+dkm_status soft_fail(dkm_status s, const char* msg, cudaError_t e = cudaSuccess) {
+  std::string m = msg;
+  if (e != cudaSuccess) {
+    m += ": ";
+    m += cudaGetErrorString(e);
+  }
+  dkm_set_last_error(m.c_str());
+  return s;
+}
+
+#define SOFT_CK(call)                                                         \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      cudaGetLastError();                                                     \
+      return soft_fail(DKM_ECUDA, #call, e_);                                 \
+    }                                                                         \
+  } while (0)
+
+dkm_status soft_plan(const int64_t* offsets, int B, int d, int k, SoftPlan* P) {
+  if (B < 1) return soft_fail(DKM_EINVAL, "B must be >= 1");
+  if (d != 2 && d != 3) return soft_fail(DKM_EINVAL, "d must be 2 or 3");
+  if (k < 1 || k > 1024) return soft_fail(DKM_EINVAL, "k must be in [1, 1024]");
+  if (!offsets) return soft_fail(DKM_EINVAL, "null offsets");
+  P->off.resize((size_t)B + 1);
+  cudaError_t e = cudaMemcpy(P->off.data(), offsets, sizeof(int64_t) * (B + 1), cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return soft_fail(DKM_EINVAL, "offsets not readable", e);
+  }
+  if (P->off[0] != 0) return soft_fail(DKM_EINVAL, "offsets[0] must be 0");
+  for (int b = 0; b < B; ++b) {
+    const int64_t nb = P->off[b + 1] - P->off[b];
+    if (nb < 1) return soft_fail(DKM_EINVAL, "every cloud needs at least one point");
+    P->max_n = std::max(P->max_n, nb);
+  }
+  P->n_total = P->off[B];
+  P->gx = (int)((P->max_n + kRowThreads - 1) / kRowThreads);
+  P->ns = (int)((P->max_n + kSplit - 1) / kSplit);
+  return DKM_OK;
+}
+
+// scratch laid out in one stream-ordered allocation
+struct SoftScratch {
+  void* base = nullptr;
+  SoftArgs A{};
+  double* loss_part = nullptr;
+  double* loss_dev = nullptr;
+  float* N = nullptr;
+  float* G[2] = {nullptr, nullptr};
+  int32_t* labels = nullptr;
+};
+
+dkm_status soft_alloc(const SoftPlan& P, int B, int d, int k, const float* tau, cudaStream_t st,
+                      SoftScratch* S) {
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t n = (size_t)P.n_total;
+  size_t o_off = 0, o_tau = o_off + al(sizeof(int64_t) * (B + 1)), o_m = o_tau + al(sizeof(float) * B),
+         o_iz = o_m + al(4 * n), o_aux = o_iz + al(4 * n), o_part = o_aux + al(4 * n),
+         o_lp = o_part + al(sizeof(double) * 4 * (size_t)B * P.ns * k),
+         o_ld = o_lp + al(sizeof(double) * (size_t)B * P.gx), o_N = o_ld + al(sizeof(double) * B),
+         o_G0 = o_N + al(4 * (size_t)B * k), o_G1 = o_G0 + al(4 * (size_t)B * k * d),
+         o_lab = o_G1 + al(4 * (size_t)B * k * d), total = o_lab + al(4 * n);
+  SOFT_CK(cudaMallocAsync(&S->base, total, st));
+  char* c = (char*)S->base;
+  SoftArgs& A = S->A;
+  A.off = (const int64_t*)(c + o_off);
+  A.tau = (const float*)(c + o_tau);
+  A.m = (float*)(c + o_m);
+  A.iz = (float*)(c + o_iz);
+  A.aux = (float*)(c + o_aux);
+  A.part = (double*)(c + o_part);
+  A.B = B;
+  A.k = k;
+  A.ns = P.ns;
+  S->loss_part = (double*)(c + o_lp);
+  S->loss_dev = (double*)(c + o_ld);
+  S->N = (float*)(c + o_N);
+  S->G[0] = (float*)(c + o_G0);
+  S->G[1] = (float*)(c + o_G1);
+  S->labels = (int32_t*)(c + o_lab);
+  SOFT_CK(cudaMemcpyAsync((void*)A.off, P.off.data(), sizeof(int64_t) * (B + 1),
+                          cudaMemcpyHostToDevice, st));
+  SOFT_CK(cudaMemcpyAsync((void*)A.tau, tau, sizeof(float) * B, cudaMemcpyDefault, st));
+  return DKM_OK;
+}
+
+template <int D, int MODE>
+void launch_row(const SoftScratch& S, const SoftPlan& P, const float* Ct, const float* Cn,
+                const float* Nn, const float* Gn, const double* dloss, float* gP, int32_t* lab,
+                cudaStream_t st) {
+  const size_t smem = sizeof(float4) * (size_t)S.A.k * (MODE == kRowStep ? 3 : 1);
+  k_soft_row<D, MODE><<<dim3(P.gx, S.A.B), kRowThreads, smem, st>>>(S.A, Ct, Cn, Nn, Gn, dloss, gP,
+                                                                   lab, S.loss_part);
+}
+
+template <int D, int MODE>
+void launch_col(const SoftScratch& S, const SoftPlan& P, const float* Ct, const float* Cn,
+                const float* Nn, const float* Gn, const double* dloss, const int32_t* lab,
+                cudaStream_t st) {
+  const int thr = std::max(32, (S.A.k + 31) / 32 * 32);
+  k_soft_col<D, MODE><<<dim3(P.ns, S.A.B), thr, 0, st>>>(S.A, Ct, Cn, Nn, Gn, dloss, lab);
+}
+
+void launch_reduce(const SoftScratch& S, int d, int mode, const float* Ct, float* Cnext, float* Nout,
+                   float* Gout, cudaStream_t st) {
+  const int64_t tot = (int64_t)S.A.B * S.A.k;
+  k_soft_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(S.A, d, mode, Ct, Cnext, Nout, Gout);
+}
+
+dkm_status finish_loss(const SoftScratch& S, const SoftPlan& P, int B, double* loss, cudaStream_t st) {
+  k_soft_loss<<<(B + 127) / 128, 128, 0, st>>>(S.loss_part, P.gx, B, S.loss_dev);
+  SOFT_CK(cudaGetLastError());
+  if (loss) {
+    SOFT_CK(cudaMemcpyAsync(loss, S.loss_dev, sizeof(double) * B, cudaMemcpyDefault, st));
+  }
+  return DKM_OK;
+}
+
+template <int D>
+dkm_status soft_forward_impl(const float* pts, const SoftPlan& P, int B, int k, const float* init,
+                             int T, const float* tau, float* ckpt, double* loss, cudaStream_t st) {
+  SoftScratch S;
+  dkm_status r = soft_alloc(P, B, D, k, tau, st, &S);
+  if (r != DKM_OK) return r;
+  S.A.P = pts;
+  const size_t ck = (size_t)B * k * D;   // floats per checkpoint
+  SOFT_CK(cudaMemcpyAsync(ckpt, init, sizeof(float) * ck, cudaMemcpyDefault, st));
+  for (int t = 0; t < T; ++t) {
+    const float* Ct = ckpt + t * ck;
+    launch_row<D, kRowStats>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_col<D, kColMean>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_reduce(S, D, 0, Ct, ckpt + (t + 1) * ck, nullptr, nullptr, st);
+  }
+  launch_row<D, kRowLoss>(S, P, ckpt + T * ck, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          st);
+  r = finish_loss(S, P, B, loss, st);
+  cudaFreeAsync(S.base, st);
+  if (r != DKM_OK) return r;
+  SOFT_CK(cudaGetLastError());
+  SOFT_CK(cudaStreamSynchronize(st));
+  return DKM_OK;
+}
+
+template <int D>
+dkm_status soft_backward_impl(const float* pts, const SoftPlan& P, int B, int k, const float* ckpt,
+                              int T, const float* tau, const double* dloss, float* gp, float* gi,
+                              cudaStream_t st) {
+  SoftScratch S;
+  dkm_status r = soft_alloc(P, B, D, k, tau, st, &S);
+  if (r != DKM_OK) return r;
+  S.A.P = pts;
+  double* dl = S.loss_dev;   // upstream gradient per cloud, on the device
+  SOFT_CK(cudaMemcpyAsync(dl, dloss, sizeof(double) * B, cudaMemcpyDefault, st));
+  const size_t ck = (size_t)B * k * D;
+  // loss stage
+  const float* CT = ckpt + T * ck;
+  launch_row<D, kRowLossBwd>(S, P, CT, nullptr, nullptr, nullptr, dl, gp, nullptr, st);
+  launch_col<D, kColLoss>(S, P, CT, nullptr, nullptr, nullptr, dl, nullptr, st);
+  int cur = 0;
+  launch_reduce(S, D, 1, CT, nullptr, nullptr, S.G[cur], st);
+  // the updates, last first
+  for (int t = T - 1; t >= 0; --t) {
+    const float* Ct = ckpt + t * ck;
+    const float* Cn = ckpt + (t + 1) * ck;
+    launch_row<D, kRowStats>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_col<D, kColMean>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_reduce(S, D, 0, Ct, nullptr, S.N, nullptr, st);
+    launch_row<D, kRowStep>(S, P, Ct, Cn, S.N, S.G[cur], nullptr, gp, nullptr, st);
+    launch_col<D, kColStep>(S, P, Ct, Cn, S.N, S.G[cur], nullptr, nullptr, st);
+    launch_reduce(S, D, 1, Ct, nullptr, nullptr, S.G[cur ^ 1], st);
+    cur ^= 1;
+  }
+  SOFT_CK(cudaMemcpyAsync(gi, S.G[cur], sizeof(float) * ck, cudaMemcpyDefault, st));
+  cudaFreeAsync(S.base, st);
+  SOFT_CK(cudaGetLastError());
+  SOFT_CK(cudaStreamSynchronize(st));
+  return DKM_OK;
+}
+
+template <int D>
+dkm_status hard_impl(const float* pts, const SoftPlan& P, int B, int k, const float* C,
+                     int32_t* labels, double* loss, float* gp, float* gc, cudaStream_t st) {
+  SoftScratch S;
+  std::vector<float> ones((size_t)B, 1.f);   // the temperature is unused here
+  dkm_status r = soft_alloc(P, B, D, k, ones.data(), st, &S);
+  if (r != DKM_OK) return r;
+  S.A.P = pts;
+  int32_t* lab = labels ? labels : S.labels;
+  launch_row<D, kRowHard>(S, P, C, nullptr, nullptr, nullptr, nullptr, gp, lab, st);
+  r = finish_loss(S, P, B, loss, st);
+  if (r == DKM_OK && gc) {
+    launch_col<D, kColHard>(S, P, C, nullptr, nullptr, nullptr, nullptr, lab, st);
+    launch_reduce(S, D, 1, C, nullptr, nullptr, gc, st);
+  }
+  cudaFreeAsync(S.base, st);
+  if (r != DKM_OK) return r;
+  SOFT_CK(cudaGetLastError());
+  SOFT_CK(cudaStreamSynchronize(st));
+  return DKM_OK;
+}
+
+}  // namespace
+}  // namespace dkm
+
+using namespace dkm;
+
+extern "C" {
+
+DKM_API dkm_status dkm_soft_forward(const float* points, const int64_t* offsets, int B, int d,
+                                    int k, const float* init_centroids, int T, const float* tau,
+                                    float* ckpt, double* loss, void* stream) {
+  SoftPlan P;
+  dkm_status r = soft_plan(offsets, B, d, k, &P);
+  if (r != DKM_OK) return r;
+  if (T < 0) return soft_fail(DKM_EINVAL, "T must be >= 0");
+  if (!points || !init_centroids || !tau || !ckpt) return soft_fail(DKM_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  return d == 3 ? soft_forward_impl<3>(points, P, B, k, init_centroids, T, tau, ckpt, loss, st)
+                : soft_forward_impl<2>(points, P, B, k, init_centroids, T, tau, ckpt, loss, st);
+}
+
+DKM_API dkm_status dkm_soft_backward(const float* points, const int64_t* offsets, int B, int d,
+                                     int k, const float* ckpt, int T, const float* tau,
+                                     const double* dloss, float* grad_points, float* grad_init,
+                                     void* stream) {
+  SoftPlan P;
+  dkm_status r = soft_plan(offsets, B, d, k, &P);
+  if (r != DKM_OK) return r;
+  if (T < 0) return soft_fail(DKM_EINVAL, "T must be >= 0");
+  if (!points || !ckpt || !tau || !dloss || !grad_points || !grad_init)
+    return soft_fail(DKM_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  return d == 3 ? soft_backward_impl<3>(points, P, B, k, ckpt, T, tau, dloss, grad_points,
+                                        grad_init, st)
+                : soft_backward_impl<2>(points, P, B, k, ckpt, T, tau, dloss, grad_points,
+                                        grad_init, st);
+}
+
+DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int B, int d, int k,
+                                const float* centroids, int32_t* labels, double* loss,
+                                float* grad_points, float* grad_centroids, void* stream) {
+  SoftPlan P;
+  dkm_status r = soft_plan(offsets, B, d, k, &P);
+  if (r != DKM_OK) return r;
+  if (!points || !centroids) return soft_fail(DKM_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  return d == 3 ? hard_impl<3>(points, P, B, k, centroids, labels, loss, grad_points,
+                               grad_centroids, st)
+                : hard_impl<2>(points, P, B, k, centroids, labels, loss, grad_points,
+                               grad_centroids, st);
+}
+
+}  // extern "C"

@@ -93,6 +93,18 @@ _SIGS = [
                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_void_p]),
+    ("dkm_soft_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    ("dkm_soft_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    ("dkm_hard_sse", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
 ]
 
 DKM_NOALLOC_MAX_K = 65536
@@ -124,7 +136,8 @@ def _arr(x: Any, dtype: str, numel: Optional[int] = None, name: str = "array"):
     if x is None:
         return None, None
     if hasattr(x, "data_ptr"):   # torch.Tensor
-        want = {"float32": "torch.float32", "int32": "torch.int32"}[dtype]
+        want = {"float32": "torch.float32", "int32": "torch.int32", "int64": "torch.int64",
+                "float64": "torch.float64"}[dtype]
         if str(x.dtype) != want:
             raise TypeError(f"{name} must be {want}, got {x.dtype}")
         if not x.is_contiguous():
@@ -280,6 +293,48 @@ def dkm_last_stats(ctx: Context) -> dkm_stats:
 
 def dkm_destroy(ctx: Context) -> None:
     ctx.close()
+
+
+def dkm_soft_forward(points, offsets, B: int, d: int, k: int, init_centroids, T: int, tau, ckpt,
+                     loss, stream: int = 0) -> None:
+    """Soft k-means loss of B clouds; fills ckpt ((T+1) x B x k x d) and loss (B)."""
+    off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
+    n_total = int(offsets[-1])
+    p, _k1 = _arr(points, "float32", n_total * d, "points")
+    c0, _k2 = _arr(init_centroids, "float32", B * k * d, "init_centroids")
+    tv, _k3 = _arr(tau, "float32", B, "tau")
+    ck, _k4 = _arr(ckpt, "float32", (T + 1) * B * k * d, "ckpt")
+    ls, _k5 = _arr(loss, "float64", B, "loss")
+    _check(lib().dkm_soft_forward(p, off, B, d, k, c0, int(T), tv, ck, ls,
+                                  ctypes.c_void_p(stream or 0)), "dkm_soft_forward")
+
+
+def dkm_soft_backward(points, offsets, B: int, d: int, k: int, ckpt, T: int, tau, dloss,
+                      grad_points, grad_init, stream: int = 0) -> None:
+    off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
+    n_total = int(offsets[-1])
+    p, _k1 = _arr(points, "float32", n_total * d, "points")
+    ck, _k2 = _arr(ckpt, "float32", (T + 1) * B * k * d, "ckpt")
+    tv, _k3 = _arr(tau, "float32", B, "tau")
+    dl, _k4 = _arr(dloss, "float64", B, "dloss")
+    gp, _k5 = _arr(grad_points, "float32", n_total * d, "grad_points")
+    gi, _k6 = _arr(grad_init, "float32", B * k * d, "grad_init")
+    _check(lib().dkm_soft_backward(p, off, B, d, k, ck, int(T), tv, dl, gp, gi,
+                                   ctypes.c_void_p(stream or 0)), "dkm_soft_backward")
+
+
+def dkm_hard_sse(points, offsets, B: int, d: int, k: int, centroids, labels=None, loss=None,
+                 grad_points=None, grad_centroids=None, stream: int = 0) -> None:
+    off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
+    n_total = int(offsets[-1])
+    p, _k1 = _arr(points, "float32", n_total * d, "points")
+    c, _k2 = _arr(centroids, "float32", B * k * d, "centroids")
+    lab, _k3 = _arr(labels, "int32", n_total, "labels")
+    ls, _k4 = _arr(loss, "float64", B, "loss")
+    gp, _k5 = _arr(grad_points, "float32", n_total * d, "grad_points")
+    gc, _k6 = _arr(grad_centroids, "float32", B * k * d, "grad_centroids")
+    _check(lib().dkm_hard_sse(p, off, B, d, k, c, lab, ls, gp, gc, ctypes.c_void_p(stream or 0)),
+           "dkm_hard_sse")
 
 
 def dkm_lloyd_step_noalloc(points, n: int, d: int, k: int, centroids, centroids_out, labels,
