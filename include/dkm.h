@@ -203,6 +203,94 @@ DKM_API dkm_status dkm_fit(const float* points, int64_t n, int d, int k, const f
                    int max_iter, float* centroids_out, int32_t* labels_out,
                    int* iterations_out, double* sse_out, const dkm_options* opts);
 
+/*
+ * Batched contexts: B independent k-means problems ("clouds") in one
+ * context, run together -- every kernel of a pass covers the tiles of all
+ * clouds, so a pass is one launch per kernel whatever B is, and the whole
+ * loop is one CUDA graph.  Each cloud has its own point index (Morton
+ * order and tiles on its own bounding box), its own centroid grid (cells
+ * ~ cells_per_centroid * k_b, all clouds' grids together under
+ * mem_budget_bytes), its own fixed-point scale and its own early stop.
+ * The paper runs one problem at a time; a batch of B clouds gives exactly
+ * the B results of B separate runs.
+ *
+ * points: concatenated clouds, n_total x d (host or device);
+ * offsets: B + 1 int64 (host or device), offsets[0] = 0, cloud b =
+ *   rows offsets[b] .. offsets[b+1] - 1, every cloud non-empty;
+ * ks: B int32 (host or device), 1 <= ks[b] <= points of cloud b;
+ * centroid arrays (init, output): sum(ks) x d, cloud after cloud;
+ * labels: n_total int32, cloud-local centroid index (0 .. ks[b] - 1);
+ * iterations_out (B int32) and sse_out (B double), host or device,
+ *   nullable: passes executed and final SSE of each cloud.
+ * 1 <= B <= 65535.  For B > 1 the sort key keeps the cloud index in its top
+ * ceil(log2 B) bits, so each cloud's Morton code gets fewer bits per axis
+ * (7 in 3D at B = 512); the results do not depend on it.
+ * The single-cloud functions accept batched contexts too: dkm_assign
+ * returns the total SSE and change count, dkm_run the largest pass count
+ * and the total SSE, dkm_get_plan cloud 0's grid with the total cell count.
+ * Errors as dkm_create / dkm_run, plus DKM_EINVAL for bad offsets or ks.
+ */
+DKM_API dkm_status dkm_create_batched(dkm_ctx** out, const float* points, const int64_t* offsets,
+                                      int B, int d, const int32_t* ks, const dkm_options* opts);
+DKM_API dkm_status dkm_run_batched(dkm_ctx* ctx, const float* init_centroids, int max_iter,
+                                   float* centroids_out, int32_t* labels_out,
+                                   int32_t* iterations_out, double* sse_out);
+DKM_API dkm_status dkm_fit_batched(const float* points, const int64_t* offsets, int B, int d,
+                                   const int32_t* ks, const float* init_centroids, int max_iter,
+                                   float* centroids_out, int32_t* labels_out,
+                                   int32_t* iterations_out, double* sse_out,
+                                   const dkm_options* opts);
+
+/*
+ * Index tuning of a context.  None of these settings changes which centroid
+ * is nearest to a point (the labels of a given centroid set are exact
+ * whatever the index); they change how much work the pruning does.  The
+ * tile cut also regroups the per-tile fixed-point sums of the update, so
+ * centroids computed under different cuts may differ in their last bits
+ * (far inside the update's error bound).  The paper fits a cost model for
+ * its memory/leaf-capacity choice (Section V-A); here the choice is
+ * measured instead.
+ */
+typedef struct {
+    /* grid cells per centroid before the memory-budget cap, in
+     * (0, max(4, opts.cells_per_centroid)] */
+    float cells_per_centroid;
+    /* a cloud's tiles are cut at the finest Morton cubes that add at most
+     * its 256-point windows / tile_cut_div tiles; 2 .. 1024 (default 8) */
+    int tile_cut_div;
+    /* tile candidate lists longer than this are filtered again per row of
+     * 64 points (default 48; >= 256 turns the row filter off) */
+    int row_filter_min;
+    /* dkm_autotune only: mean ms per Lloyd pass of the chosen setting and
+     * of the setting the context had before, configurations timed, and
+     * whether the choice came from the process-wide cache (nothing timed) */
+    float ms_per_pass;
+    float ms_per_pass_before;
+    int trials;
+    int from_cache;
+} dkm_tuning;
+
+/* Current setting of a context (timing fields 0). */
+DKM_API dkm_status dkm_get_tuning(const dkm_ctx* ctx, dkm_tuning* out);
+
+/* Apply a setting (the timing fields are ignored); re-plans the grids and
+ * re-cuts the tiles as needed.  DKM_EINVAL for values out of range. */
+DKM_API dkm_status dkm_set_tuning(dkm_ctx* ctx, const dkm_tuning* tuning);
+
+/*
+ * Measure and apply the fastest setting for this context: coordinate
+ * descent over cells_per_centroid {0.5, 1, 2, 4}, tile_cut_div
+ * {2, 4, 8, 16, 32} and row_filter_min {16, 32, 48, 96, 256}, each
+ * setting timed (CUDA events, best of two) over `passes` Lloyd passes
+ * (1 .. 64, no early stop) from init_centroids.  The context's labels and
+ * centroids are overwritten by those runs.  With use_cache = 1 a setting
+ * found before in this process for the same workload shape (d, number of
+ * clouds, and the rounded log2 of the mean points and centroids per cloud)
+ * is applied without timing.  out (nullable) receives the choice.
+ */
+DKM_API dkm_status dkm_autotune(dkm_ctx* ctx, const float* init_centroids, int passes,
+                                int use_cache, dkm_tuning* out);
+
 /* Device bytes the context owns, and how many of them are the per-iteration
  * centroid index.  Either pointer may be NULL. */
 DKM_API dkm_status dkm_query_memory(const dkm_ctx* ctx, size_t* device_bytes, size_t* index_bytes);

@@ -3,11 +3,15 @@
 // Host code only: argument checks, the device arena of a context, the grid
 // planner (the memory-tunable index of Section V-A), and the Lloyd loop of
 // Algorithm 1 captured once per (context, max_iter) as a CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "dkm_host.h"
 
@@ -44,6 +48,9 @@ dkm_status fail(dkm_status s, const char* fmt, ...) {
 
 constexpr size_t kDefaultBudget = size_t(64) << 20;
 constexpr int64_t kMaxPoints = (int64_t(1) << 31) - kBlockPts;
+constexpr int kMaxClouds = 65535;        // grid.y limit of the per-cloud box kernel
+constexpr float kTuneMaxCpc = 4.0f;      // densest grid the arena is sized for
+constexpr int kMinCutDiv = 2;            // most tile cuts the arena is sized for
 
 // true for memory a kernel may dereference directly (device or managed)
 bool is_device_ptr(const void* p) {
@@ -70,27 +77,54 @@ dkm_options resolve(const dkm_options* o) {
   return r;
 }
 
-// bytes of the per-iteration centroid index for a grid of `cells`
-size_t index_bytes_for(int64_t cells, int k, int cap) {
-  return size_t(2) * cells * (sizeof(int) + size_t(cap) * sizeof(float4)) +
-         size_t(2) * k * sizeof(float4) + 2 * sizeof(int);
+size_t per_cell_bytes(int cap) { return size_t(2) * (sizeof(int) + size_t(cap) * sizeof(float4)); }
+
+// bytes of the per-iteration centroid index for grids of `cells` in all
+size_t index_bytes_for(int64_t cells, int64_t k, int cap) {
+  return size_t(cells) * per_cell_bytes(cap) + size_t(2) * k * sizeof(float4) + 2 * sizeof(int);
 }
 
-// Plan the grid; *max_cells = the cell count any point set of this (n, k,
-// budget) can need, which sizes the arena.
-dkm_status plan_grid(int64_t n, int d, int k, const float* lo, const float* hi,
-                     const dkm_options& o, dkm_plan_info* out, int64_t* max_cells) {
+// Cells per cloud under the memory budget (the memory-tunable index of
+// Section V-A): ceil(cpc * k_b) each, scaled down together until the grids
+// of all clouds fit the budget (at least one cell per cloud).
+dkm_status cell_targets(const std::vector<int>& ks, float cpc, size_t budget,
+                        std::vector<int64_t>* tgt, int64_t* total) {
   const int cap = kBucketCap;
-  const size_t per_cell = size_t(2) * (sizeof(int) + size_t(cap) * sizeof(float4));
-  const size_t fixed = index_bytes_for(0, k, cap);
-  if (o.mem_budget_bytes < fixed + per_cell)
-    return fail(DKM_ENOMEM, "memory budget %zu B cannot hold the centroid index of k=%d (needs >= %zu B)",
-                o.mem_budget_bytes, k, fixed + per_cell);
-  int64_t budget_cells = (int64_t)((o.mem_budget_bytes - fixed) / per_cell);
-  int64_t target = (int64_t)std::ceil((double)o.cells_per_centroid * (double)k);
-  if (target < 1) target = 1;
-  if (target > budget_cells) target = budget_cells;
-  if (target > (int64_t(1) << 28)) target = int64_t(1) << 28;
+  const int64_t B = (int64_t)ks.size();
+  int64_t K = 0;
+  for (int kb : ks) K += kb;
+  const size_t fixed = index_bytes_for(0, K, cap);
+  const size_t need = fixed + size_t(B) * per_cell_bytes(cap);
+  if (budget < need)
+    return fail(DKM_ENOMEM, "memory budget %zu B cannot hold the centroid index of k=%lld (needs >= %zu B)",
+                budget, (long long)K, need);
+  const int64_t budget_cells = (int64_t)((budget - fixed) / per_cell_bytes(cap));
+  tgt->assign(B, 1);
+  int64_t sum = 0;
+  for (int64_t b = 0; b < B; ++b) {
+    int64_t t = (int64_t)std::ceil((double)cpc * (double)ks[b]);
+    t = std::min<int64_t>(std::max<int64_t>(t, 1), int64_t(1) << 28);
+    (*tgt)[b] = t;
+    sum += t;
+  }
+  if (sum > budget_cells) {
+    // t' = 1 + floor((t - 1) f) with f = (budget_cells - B) / (sum - B):
+    // sum t' <= budget_cells and t' >= 1
+    const double f = (double)(budget_cells - B) / (double)(sum - B);
+    sum = 0;
+    for (int64_t b = 0; b < B; ++b) {
+      (*tgt)[b] = 1 + (int64_t)std::floor((double)((*tgt)[b] - 1) * f);
+      sum += (*tgt)[b];
+    }
+  }
+  *total = sum;
+  return DKM_OK;
+}
+
+// Uniform grid over [lo, hi] with at most `target` cells: cell edge s,
+// cells per axis dims.
+void grid_geometry(int d, const float* lo, const float* hi, int64_t target, int64_t dims[3],
+                   double* s_out) {
   double E[3] = {0, 0, 0};
   int deff = 0;
   double vol = 1.0;
@@ -102,7 +136,7 @@ dkm_status plan_grid(int64_t n, int d, int k, const float* lo, const float* hi,
     }
   }
   double s = 1.0;
-  int64_t dims[3] = {1, 1, 1};
+  dims[0] = dims[1] = dims[2] = 1;
   if (deff > 0) {
     s = std::pow(vol / (double)target, 1.0 / deff);
     if (!(s > 0)) s = 1e-30;
@@ -117,20 +151,7 @@ dkm_status plan_grid(int64_t n, int d, int k, const float* lo, const float* hi,
       s *= 1.02;
     }
   }
-  memset(out, 0, sizeof(*out));
-  int64_t cells = 1;
-  for (int a = 0; a < 3; ++a) {
-    out->dims[a] = (int)dims[a];
-    out->origin[a] = a < d ? lo[a] : 0.f;
-    cells *= dims[a];
-  }
-  out->cell = (float)s;
-  out->bucket_cap = cap;
-  out->cells = cells;
-  out->index_bytes = index_bytes_for(cells, k, cap);
-  *max_cells = target;
-  (void)n;
-  return DKM_OK;
+  *s_out = s;
 }
 
 struct Layout {
@@ -145,22 +166,26 @@ struct Layout {
 
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
-  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles, wcnt,
-      wbase, level_hist, lab, cw, acc, slots, st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt,
-      tlist, tcnt, cstage, cstage2, kstage, total;
+  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles,
+      tcloud, kcloud, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+      st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
+      kstage, total;
 };
 
 int64_t windows_of(int64_t n) { return (n + kTilePts - 1) / kTilePts; }
-// Cube cuts add at most one tile per cube, and the tiling level is chosen so
-// that the cubes number at most an eighth of the windows.
-int64_t tiles_max_of(int64_t n) { return windows_of(n) + windows_of(n) / 8 + 2; }
+// Tiles of B clouds: every window, plus at most B - 1 cloud cuts, plus the
+// cube cuts, which the tiling level keeps to max(1, windows_b / cut_div)
+// per cloud (windows_b summing to at most windows + B).
+int64_t tiles_cap_of(int64_t n, int64_t B) {
+  return windows_of(n) + windows_of(n) / kMinCutDiv + 3 * B + 2;
+}
 
-ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
+ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, int cap) {
   ArenaPlan P;
   Layout L;
   const int64_t nb = (n + kBlockPts - 1) / kBlockPts;
   const int64_t n_pad = nb * kBlockPts;
-  const int64_t nw = windows_of(n), tm = tiles_max_of(n);
+  const int64_t nw = windows_of(n), tm = tiles_cap_of(n, B);
   P.xs = L.take<float>(n_pad);
   P.ys = L.take<float>(n_pad);
   P.zs = L.take<float>(d == 3 ? n_pad : 1);
@@ -173,9 +198,16 @@ ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
   P.tbox = L.take<float4>(2 * tm);
   P.tiles = L.take<int2>(tm);
   P.n_tiles = L.take<int>(1);
+  P.tcloud = L.take<int>(tm);
+  P.kcloud = L.take<int>(k);
   P.wcnt = L.take<int>(nw);
   P.wbase = L.take<int>(nw);
-  P.level_hist = L.take<unsigned long long>(kMaxLevels + 1);
+  P.level_hist = L.take<unsigned long long>(B * (kMaxLevels + 1));
+  P.doff = L.take<int64_t>(B + 1);
+  P.dcoff = L.take<int64_t>(B + 1);
+  P.clouds = L.take<Cloud>(B);
+  P.crun = L.take<CloudRun>(B);
+  P.cacc = L.take<CloudAcc>(B);
   P.lab = L.take<int32_t>(n_pad);
   P.cw = L.take<float4>(k);
   P.acc = L.take<Acc>(k);
@@ -187,7 +219,8 @@ ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
   P.gbkt1 = L.take<float4>(max_cells * cap);
   P.ovf0 = L.take<float4>(k);
   P.ovf1 = L.take<float4>(k);
-  P.ovf_cnt = L.take<int>(2);
+  P.ovf_cnt0 = L.take<int>(B);
+  P.ovf_cnt1 = L.take<int>(B);
   P.tlist = L.take<int>(tm * kTileCap);
   P.tcnt = L.take<int>(tm);
   P.cstage = L.take<float>((size_t)k * d);
@@ -197,15 +230,29 @@ ArenaPlan arena_plan(int64_t n, int d, int k, int64_t max_cells, int cap) {
   return P;
 }
 
+// grid cells the arena holds: the budget-capped targets of the densest
+// grid the context may use (the tuner tries up to kTuneMaxCpc)
+dkm_status cell_capacity(const std::vector<int>& ks, const dkm_options& o, int64_t* cap) {
+  std::vector<int64_t> tgt;
+  return cell_targets(ks, std::max(o.cells_per_centroid, kTuneMaxCpc), o.mem_budget_bytes, &tgt,
+                      cap);
+}
+
 IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   IterArgs A;
   memset(&A, 0, sizeof(A));
   A.n = c->n;
   A.k = c->k;
+  A.B = c->B;
   A.n_windows = c->n_windows;
-  A.tiles_max = c->tiles_max;
-  A.n_tiles = c->n_tiles_dev;
+  A.n_tiles = c->n_tiles;
   A.tiles = c->tiles;
+  A.tcloud = c->tcloud;
+  A.kcloud = c->kcloud;
+  A.clouds = c->clouds;
+  A.cl0 = c->h_clouds[0];
+  A.crun = c->crun;
+  A.cacc = c->cacc;
   A.xs = c->xs;
   A.ys = c->ys;
   A.zs = c->zs;
@@ -215,13 +262,13 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.acc = c->acc;
   A.slots = c->slots;
   A.st = c->st;
-  A.grid = c->grid;
+  A.total_cells = c->total_cells;
   for (int p = 0; p < 2; ++p) {
     A.gcnt[p] = c->gcnt[p];
     A.gbkt[p] = c->gbkt[p];
     A.ovf[p] = c->ovf[p];
+    A.ovf_cnt[p] = c->ovf_cnt[p];
   }
-  A.ovf_cnt = c->ovf_cnt;
   A.tlist = c->tlist;
   A.tcnt = c->tcnt;
   A.sse_hist = c->sse_hist;
@@ -253,6 +300,21 @@ dkm_status read_state(dkm_ctx* c, DevState* h) {
   return DKM_OK;
 }
 
+dkm_status read_clouds(dkm_ctx* c, std::vector<CloudRun>* h) {
+  h->resize(c->B);
+  DKM_CK(cudaMemcpyAsync(h->data(), c->crun, sizeof(CloudRun) * c->B, cudaMemcpyDeviceToHost,
+                         c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  return DKM_OK;
+}
+
+dkm_status upload_clouds(dkm_ctx* c) {
+  DKM_CK(cudaMemcpyAsync(c->clouds, c->h_clouds.data(), sizeof(Cloud) * c->B,
+                         cudaMemcpyHostToDevice, c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  return DKM_OK;
+}
+
 // Copy a k x d centroid array (host or device) into the context's staging.
 dkm_status stage_centroids(dkm_ctx* c, const float* C) {
   size_t bytes = (size_t)c->k * c->d * sizeof(float);
@@ -267,9 +329,12 @@ dkm_status ensure_lstage(dkm_ctx* c) {
   return DKM_OK;
 }
 
-// centroid bbox of the staged centroids (for the fixed-point scale) + check
+// per-cloud bbox of the staged centroids, then the fixed-point exponents
+// of every cloud; optional non-finite check
 dkm_status centroid_box(dkm_ctx* c, bool check) {
-  DKM_CK(launch_bbox(c->cstage, c->k, c->d, c->st, 1, c->d, c->stream));
+  DKM_CK(launch_bbox(c->cstage, c->d, c->dcoff, c->B, c->max_k_b, c->crun, c->st, 1, c->d,
+                     c->stream));
+  DKM_CK(launch_exponents(c->clouds, c->crun, c->B, c->stream));
   if (check) {
     DevState h;
     DKM_TRY(read_state(c, &h));
@@ -279,15 +344,25 @@ dkm_status centroid_box(dkm_ctx* c, bool check) {
 }
 
 dkm_status zero_run_buffers(dkm_ctx* c, bool labels_to_minus_one) {
-  DKM_CK(launch_reset_run(c->st, c->stream));
+  IterArgs A = iter_args(c, 0, 0);
+  DKM_CK(launch_reset_run(A, c->stream));
   DKM_CK(cudaMemsetAsync(c->acc, 0, (size_t)c->k * sizeof(Acc), c->stream));
   DKM_CK(cudaMemsetAsync(c->slots, 0, (size_t)kSlots * sizeof(Slot), c->stream));
-  DKM_CK(cudaMemsetAsync(c->gcnt[0], 0, (size_t)c->max_cells * sizeof(int), c->stream));
-  DKM_CK(cudaMemsetAsync(c->gcnt[1], 0, (size_t)c->max_cells * sizeof(int), c->stream));
-  DKM_CK(cudaMemsetAsync(c->ovf_cnt, 0, 2 * sizeof(int), c->stream));
+  DKM_CK(cudaMemsetAsync(c->gcnt[0], 0, (size_t)c->total_cells * sizeof(int), c->stream));
+  DKM_CK(cudaMemsetAsync(c->gcnt[1], 0, (size_t)c->total_cells * sizeof(int), c->stream));
+  DKM_CK(cudaMemsetAsync(c->ovf_cnt[0], 0, (size_t)c->B * sizeof(int), c->stream));
+  DKM_CK(cudaMemsetAsync(c->ovf_cnt[1], 0, (size_t)c->B * sizeof(int), c->stream));
   if (labels_to_minus_one)
     DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
   return DKM_OK;
+}
+
+void destroy_graph(dkm_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->g_iters = -1;
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
 }
 
 dkm_status ensure_hist(dkm_ctx* c, int iters) {
@@ -301,20 +376,8 @@ dkm_status ensure_hist(dkm_ctx* c, int iters) {
   DKM_CK(cudaMalloc(&c->sse_hist, (size_t)cap * sizeof(double)));
   DKM_CK(cudaMalloc(&c->chg_hist, (size_t)cap * sizeof(unsigned long long)));
   c->hist_cap = cap;
-  if (c->gexec) {   // the cached graph holds the old pointers
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-    c->g_iters = -1;
-  }
+  destroy_graph(c);   // the cached graph holds the old pointers
   return DKM_OK;
-}
-
-void destroy_graph(dkm_ctx* c) {
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  c->gexec = nullptr;
-  c->g_iters = -1;
-  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  c->ev.clear();
 }
 
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
@@ -339,7 +402,9 @@ dkm_status one_pass(dkm_ctx* c, bool track_changes) {
   return DKM_OK;
 }
 
-// labels (sorted, device) -> caller array in original order
+// labels (sorted, device) -> caller array in original order (cloud-local
+// indices); with do_sse the per-cloud SSE of those labels is left in the
+// pass counters for a t = -2 collect
 dkm_status export_labels(dkm_ctx* c, int32_t* labels, bool do_sse) {
   IterArgs A = iter_args(c, 0, 0);
   int32_t* dst = nullptr;
@@ -433,6 +498,544 @@ dkm_status validate_sizes(int64_t n, int d, int k) {
   return DKM_OK;
 }
 
+dkm_status validate_batch(const std::vector<int64_t>& off, const std::vector<int>& ks, int d) {
+  const int B = (int)ks.size();
+  if (d != 2 && d != 3) return fail(DKM_EINVAL, "d must be 2 or 3 (got %d)", d);
+  if (B < 1 || B > kMaxClouds) return fail(DKM_EINVAL, "B must be in [1, %d] (got %d)", kMaxClouds, B);
+  if (off[0] != 0) return fail(DKM_EINVAL, "offsets[0] must be 0");
+  int64_t K = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t nb = off[b + 1] - off[b];
+    if (nb < 1) return fail(DKM_EINVAL, "cloud %d is empty (offsets must increase)", b);
+    if (ks[b] < 1) return fail(DKM_EINVAL, "k of cloud %d must be >= 1 (got %d)", b, ks[b]);
+    if ((int64_t)ks[b] > nb)
+      return fail(DKM_EINVAL, "k of cloud %d (%d) exceeds its %lld points", b, ks[b], (long long)nb);
+    K += ks[b];
+  }
+  if (off[B] > kMaxPoints) return fail(DKM_EINVAL, "at most %lld points in all (got %lld)",
+                                       (long long)kMaxPoints, (long long)off[B]);
+  if (K > kMaxPoints) return fail(DKM_EINVAL, "too many centroids in all (%lld)", (long long)K);
+  return DKM_OK;
+}
+
+// Grid geometry of every cloud from its point box at the context's cells
+// per centroid, under the memory budget; fills the cloud table (host copy)
+// and the plan summary.
+dkm_status plan_clouds(dkm_ctx* c, const std::vector<float>& blo, const std::vector<float>& bhi) {
+  std::vector<int64_t> tgt;
+  int64_t tot = 0;
+  DKM_TRY(cell_targets(c->ks, c->cpc, c->opts.mem_budget_bytes, &tgt, &tot));
+  int64_t cell0 = 0;
+  for (int b = 0; b < c->B; ++b) {
+    int64_t dims[3];
+    double sz;
+    grid_geometry(c->d, &blo[3 * b], &bhi[3 * b], tgt[b], dims, &sz);
+    Grid g{};
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      g.g0[a] = a < c->d ? blo[3 * b + a] : 0.f;
+      g.dims[a] = (int)dims[a];
+      cells *= dims[a];
+    }
+    g.inv_s = 1.0f / (float)sz;
+    g.cap = kBucketCap;
+    g.cells = cells;
+    c->h_clouds[b].grid = g;
+    c->h_clouds[b].cell0 = cell0;
+    cell0 += cells;
+    if (b == 0) {
+      for (int a = 0; a < 3; ++a) {
+        c->plan.dims[a] = (int)dims[a];
+        c->plan.origin[a] = g.g0[a];
+      }
+      c->plan.cell = (float)sz;
+    }
+  }
+  if (cell0 > c->max_cells) return fail(DKM_EINTERNAL, "grid plan exceeds the arena");
+  c->total_cells = cell0;
+  c->plan.bucket_cap = kBucketCap;
+  c->plan.cells = cell0;
+  c->plan.index_bytes = index_bytes_for(cell0, c->k, kBucketCap);
+  c->plan.scratch_bytes = c->arena_bytes;
+  return DKM_OK;
+}
+
+// Tiles from the level histogram: per cloud the finest Morton level whose
+// cubes cut its sorted run into at most max(1, windows_b / cut_div) pieces
+// (so cube cuts add few tiles), then tile ranges, boxes and the tile ->
+// cloud map.
+dkm_status apply_tiling(dkm_ctx* c) {
+  const int L = c->mb;
+  for (int b = 0; b < c->B; ++b) {
+    const unsigned long long* h = &c->h_level_hist[(size_t)b * (kMaxLevels + 1)];
+    const int64_t nw_b = windows_of(c->h_clouds[b].n);
+    const unsigned long long seg_cap =
+        (unsigned long long)std::max<int64_t>(1, nw_b / c->cut_div);
+    int level = 0;
+    unsigned long long segs = 1;
+    for (int l = 1; l <= L; ++l) {
+      segs += h[l];
+      if (segs > seg_cap) break;
+      level = l;
+    }
+    c->h_clouds[b].shift = c->d * (L - level);
+    if (b == 0) c->tile_level = level;
+  }
+  DKM_TRY(upload_clouds(c));
+  DKM_CK(launch_tiles(c->skeys, c->n, c->clouds, c->d, c->mb, c->B, c->n_windows, c->wcnt,
+                      c->wbase, c->n_tiles_dev, c->tiles, c->stream));
+  int nt = 0;
+  DKM_CK(cudaMemcpyAsync(&nt, c->n_tiles_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  if (nt < 1 || nt > c->tiles_cap) return fail(DKM_EINTERNAL, "tile count %d out of range", nt);
+  c->n_tiles = nt;
+  DKM_CK(launch_tile_boxes(c->xs, c->ys, c->zs, c->d, c->tiles, nt, c->skeys, c->mb, c->B,
+                           c->tbox, c->tcloud, c->clouds, c->stream));
+  // the kernel filled each cloud's first tile: refresh the host copy
+  DKM_CK(cudaMemcpyAsync(c->h_clouds.data(), c->clouds, sizeof(Cloud) * c->B,
+                         cudaMemcpyDeviceToHost, c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  return DKM_OK;
+}
+
+// the point boxes of the last dkm_setup, per cloud (3 floats each)
+void cloud_boxes(dkm_ctx* c, const std::vector<CloudRun>& hr, std::vector<float>* lo,
+                 std::vector<float>* hi) {
+  lo->assign(3 * c->B, 0.f);
+  hi->assign(3 * c->B, 0.f);
+  for (int b = 0; b < c->B; ++b)
+    for (int a = 0; a < c->d; ++a) {
+      (*lo)[3 * b + a] = float_of(hr[b].pbox[a]);
+      (*hi)[3 * b + a] = float_of(hr[b].pbox[3 + a]);
+    }
+}
+
+dkm_status setup_impl(dkm_ctx* c, const float* points) {
+  c->ready = false;
+  c->acc_valid = false;
+  destroy_graph(c);
+  const float* src = points;
+  if (!is_device_ptr(points)) {
+    if (!c->pstage) DKM_CK(cudaMalloc(&c->pstage, (size_t)c->n * c->d * sizeof(float)));
+    DKM_CK(cudaMemcpyAsync(c->pstage, points, (size_t)c->n * c->d * sizeof(float),
+                           cudaMemcpyHostToDevice, c->stream));
+    src = c->pstage;
+  }
+  if (c->opts.profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
+  DKM_CK(launch_bbox(src, c->d, c->doff, c->B, c->max_n_b, c->crun, c->st, 0, c->d, c->stream));
+  DevState h;
+  DKM_TRY(read_state(c, &h));
+  if (h.bad) return fail(DKM_EINVAL, "points contain a non-finite or |x| > 1e18 coordinate");
+  std::vector<CloudRun> hr;
+  DKM_TRY(read_clouds(c, &hr));
+  cloud_boxes(c, hr, &c->h_blo, &c->h_bhi);
+  const std::vector<float>& blo = c->h_blo;
+  const std::vector<float>& bhi = c->h_bhi;
+  // Morton lattice of each cloud: a cube of (2^mb - 1) steps over its box
+  const float qmax = (float)((1u << c->mb) - 1u);
+  for (int b = 0; b < c->B; ++b) {
+    float emax = 0.f;
+    for (int a = 0; a < c->d; ++a) emax = std::max(emax, bhi[3 * b + a] - blo[3 * b + a]);
+    for (int a = 0; a < 3; ++a) c->h_clouds[b].mlo[a] = blo[3 * b + a];
+    c->h_clouds[b].minv = emax > 0.f ? qmax / emax : 0.f;
+  }
+  DKM_TRY(plan_clouds(c, blo, bhi));
+  DKM_TRY(upload_clouds(c));
+  DKM_CK(launch_morton(src, c->n, c->d, c->doff, c->B, c->clouds, c->mb, c->keys[0], c->vals[0],
+                       c->stream));
+  int fin = 0;
+  DKM_CK(launch_radix_sort(c->keys, c->vals, c->n, c->key_bits, c->rs_counts, c->rs_totals, &fin,
+                           c->stream));
+  c->perm = c->vals[fin];
+  c->skeys = c->keys[fin];
+  DKM_CK(launch_gather(src, c->n, c->d, c->perm, c->xs, c->ys, c->zs, c->n_pad, c->stream));
+  DKM_CK(launch_levels(c->skeys, c->n, c->d, c->mb, c->B, c->level_hist, c->stream));
+  c->h_level_hist.assign((size_t)c->B * (kMaxLevels + 1), 0ull);
+  DKM_CK(cudaMemcpyAsync(c->h_level_hist.data(), c->level_hist,
+                         sizeof(unsigned long long) * c->h_level_hist.size(),
+                         cudaMemcpyDeviceToHost, c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  DKM_TRY(apply_tiling(c));
+  DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
+  if (c->opts.profile) {
+    DKM_CK(cudaEventRecord(c->ev_b, c->stream));
+    DKM_CK(cudaEventSynchronize(c->ev_b));
+    c->timings.setup_ms = ev_ms(c->ev_a, c->ev_b);
+  }
+  c->ready = true;
+  return DKM_OK;
+}
+
+dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int64_t>& off,
+                       const std::vector<int>& ks, int d, const dkm_options* opts) {
+  *out = nullptr;
+  DKM_TRY(validate_batch(off, ks, d));
+  dkm_ctx* c = new dkm_ctx();
+  auto bail = [&](dkm_status s) {
+    dkm_destroy(c);
+    return s;
+  };
+  c->B = (int)ks.size();
+  c->n = off[c->B];
+  c->d = d;
+  c->offsets = off;
+  c->ks = ks;
+  c->coffs.assign(c->B + 1, 0);
+  for (int b = 0; b < c->B; ++b) {
+    c->coffs[b + 1] = c->coffs[b] + ks[b];
+    c->max_n_b = std::max<int64_t>(c->max_n_b, off[b + 1] - off[b]);
+    c->max_k_b = std::max<int64_t>(c->max_k_b, ks[b]);
+  }
+  c->k = (int)c->coffs[c->B];
+  c->opts = resolve(opts);
+  c->cpc = c->opts.cells_per_centroid;
+  c->row_filter_min = env_int("DKM_ROW_FILTER_MIN", 48);
+  // sort key: cloud index in the top cb bits, mb Morton bits per axis below
+  int cb = 0;
+  while ((1 << cb) < c->B) ++cb;
+  const int lmax = d == 3 ? 10 : 15;
+  c->mb = std::min(lmax, (32 - cb) / d);
+  c->key_bits = d * c->mb + cb;
+  c->h_clouds.assign(c->B, Cloud{});
+  for (int b = 0; b < c->B; ++b) {
+    c->h_clouds[b].p0 = off[b];
+    c->h_clouds[b].n = off[b + 1] - off[b];
+    c->h_clouds[b].c0 = (int)c->coffs[b];
+    c->h_clouds[b].k = ks[b];
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(DKM_ECUDA, "no CUDA device available"));
+  }
+  if (c->opts.stream) {
+    c->stream = (cudaStream_t)c->opts.stream;
+  } else {
+    if (cudaStreamCreate(&c->stream) != cudaSuccess)
+      return bail(fail(DKM_ECUDA, "cudaStreamCreate failed"));
+    c->own_stream = true;
+  }
+  c->n_blocks = (int)((c->n + kBlockPts - 1) / kBlockPts);
+  c->n_windows = (int)windows_of(c->n);
+  c->tiles_cap = (int)tiles_cap_of(c->n, c->B);
+  c->n_pad = (int64_t)c->n_blocks * kBlockPts;
+  {
+    dkm_status s = cell_capacity(ks, c->opts, &c->max_cells);
+    if (s != DKM_OK) return bail(s);
+  }
+  ArenaPlan P = arena_plan(c->n, d, c->k, c->B, c->max_cells, kBucketCap);
+  cudaError_t e = cudaMalloc(&c->arena, P.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->arena = nullptr;
+    return bail(fail(DKM_ENOMEM, "cudaMalloc(%zu B) failed: %s", P.total, cudaGetErrorString(e)));
+  }
+  c->arena_bytes = P.total;
+  char* base = (char*)c->arena;
+  c->xs = (float*)(base + P.xs);
+  c->ys = (float*)(base + P.ys);
+  c->zs = d == 3 ? (float*)(base + P.zs) : nullptr;
+  c->keys[0] = (uint32_t*)(base + P.keys0);
+  c->keys[1] = (uint32_t*)(base + P.keys1);
+  c->vals[0] = (uint32_t*)(base + P.vals0);
+  c->vals[1] = (uint32_t*)(base + P.vals1);
+  c->rs_counts = (uint32_t*)(base + P.rs_counts);
+  c->rs_totals = (uint32_t*)(base + P.rs_totals);
+  c->tbox = (float4*)(base + P.tbox);
+  c->tiles = (int2*)(base + P.tiles);
+  c->n_tiles_dev = (int*)(base + P.n_tiles);
+  c->tcloud = (int*)(base + P.tcloud);
+  c->kcloud = (int*)(base + P.kcloud);
+  c->wcnt = (int*)(base + P.wcnt);
+  c->wbase = (int*)(base + P.wbase);
+  c->level_hist = (unsigned long long*)(base + P.level_hist);
+  c->doff = (int64_t*)(base + P.doff);
+  c->dcoff = (int64_t*)(base + P.dcoff);
+  c->clouds = (Cloud*)(base + P.clouds);
+  c->crun = (CloudRun*)(base + P.crun);
+  c->cacc = (CloudAcc*)(base + P.cacc);
+  c->lab = (int32_t*)(base + P.lab);
+  c->cw = (float4*)(base + P.cw);
+  c->acc = (Acc*)(base + P.acc);
+  c->slots = (Slot*)(base + P.slots);
+  c->st = (DevState*)(base + P.st);
+  c->gcnt[0] = (int*)(base + P.gcnt0);
+  c->gcnt[1] = (int*)(base + P.gcnt1);
+  c->gbkt[0] = (float4*)(base + P.gbkt0);
+  c->gbkt[1] = (float4*)(base + P.gbkt1);
+  c->ovf[0] = (float4*)(base + P.ovf0);
+  c->ovf[1] = (float4*)(base + P.ovf1);
+  c->ovf_cnt[0] = (int*)(base + P.ovf_cnt0);
+  c->ovf_cnt[1] = (int*)(base + P.ovf_cnt1);
+  c->tlist = (int*)(base + P.tlist);
+  c->tcnt = (int*)(base + P.tcnt);
+  c->cstage = (float*)(base + P.cstage);
+  c->cstage2 = (float*)(base + P.cstage2);
+  c->kstage = (int32_t*)(base + P.kstage);
+  std::vector<int> kc(c->k);
+  for (int b = 0; b < c->B; ++b)
+    for (int64_t j = c->coffs[b]; j < c->coffs[b + 1]; ++j) kc[j] = b;
+  if (cudaMemsetAsync(c->arena, 0, P.total, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->doff, off.data(), sizeof(int64_t) * (c->B + 1), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->dcoff, c->coffs.data(), sizeof(int64_t) * (c->B + 1),
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->kcloud, kc.data(), sizeof(int) * c->k, cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaEventCreate(&c->ev_a) != cudaSuccess || cudaEventCreate(&c->ev_b) != cudaSuccess ||
+      cudaEventCreate(&c->ev_c) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(DKM_ECUDA, "context initialisation failed"));
+  }
+  dkm_status s = setup_impl(c, points);
+  if (s != DKM_OK) return bail(s);
+  *out = c;
+  return DKM_OK;
+}
+
+// Host copy of a small int64 / int32 array given as a host or device pointer.
+template <class T>
+dkm_status host_copy(const T* p, size_t count, std::vector<T>* out) {
+  out->resize(count);
+  if (is_device_ptr(p)) {
+    DKM_CK(cudaMemcpy(out->data(), p, sizeof(T) * count, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(out->data(), p, sizeof(T) * count);
+  }
+  return DKM_OK;
+}
+
+template <class T>
+dkm_status put_small(T* dst, const T* src, size_t count) {
+  if (!dst) return DKM_OK;
+  if (is_device_ptr(dst)) {
+    DKM_CK(cudaMemcpy(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+  } else {
+    memcpy(dst, src, sizeof(T) * count);
+  }
+  return DKM_OK;
+}
+
+// Lloyd's loop on every cloud of the context; leaves the run state on the
+// device and in *h.
+dkm_status run_impl(dkm_ctx* c, const float* init, int max_iter, float* centroids_out,
+                    int32_t* labels_out, DevState* h) {
+  DKM_TRY(check_ctx(c));
+  if (!init) return fail(DKM_EINVAL, "null init centroids");
+  if (max_iter < 0 || max_iter > kMaxIterCap)
+    return fail(DKM_EINVAL, "max_iter must be in [0, %d] (got %d)", kMaxIterCap, max_iter);
+  c->acc_valid = false;
+  DKM_TRY(stage_centroids(c, init));
+  DKM_TRY(centroid_box(c, true));
+  if (max_iter == 0) {
+    DKM_TRY(one_pass(c, false));
+    DKM_TRY(export_labels(c, labels_out, false));
+    DKM_TRY(export_centroids(c, centroids_out));
+    DKM_TRY(read_state(c, h));
+    DKM_TRY(check_state(*h));
+    return DKM_OK;
+  }
+  DKM_TRY(ensure_hist(c, max_iter));
+  const int early = c->opts.early_stop ? 1 : 0;
+  const int profile = c->opts.profile ? 1 : 0;
+  if (!c->gexec || c->g_iters != max_iter || c->g_algo != c->opts.algo || c->g_early != early ||
+      c->g_profile != profile)
+    DKM_TRY(build_run_graph(c, max_iter, early, profile));
+  if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
+  DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
+  if (profile) DKM_CK(cudaEventRecord(c->ev_b, c->stream));
+  // final labels in caller order + SSE of those labels against the final centroids
+  IterArgs A = iter_args(c, 0, 0);
+  DKM_TRY(export_labels(c, labels_out, true));
+  DKM_CK(launch_collect(A, -2, c->stream));
+  DKM_TRY(export_centroids(c, centroids_out));
+  if (profile) DKM_CK(cudaEventRecord(c->ev_c, c->stream));
+  DKM_TRY(read_state(c, h));
+  DKM_TRY(check_state(*h));
+  if (profile) {
+    dkm_timings& T = c->timings;
+    T.iterations_ms = ev_ms(c->ev_a, c->ev_b);
+    T.finalize_ms = ev_ms(c->ev_b, c->ev_c);
+    T.passes = h->passes;
+    double s = 0, a = 0, u = 0;
+    for (int t = 0; t < h->passes && t < max_iter; ++t) {
+      s += ev_ms(c->ev[4 * t + 0], c->ev[4 * t + 1]);
+      a += ev_ms(c->ev[4 * t + 1], c->ev[4 * t + 2]);
+      u += ev_ms(c->ev[4 * t + 2], c->ev[4 * t + 3]);
+    }
+    int p = h->passes > 0 ? h->passes : 1;
+    T.search_ms = (float)(s / p);
+    T.assign_ms = (float)(a / p);
+    T.update_ms = (float)(u / p);
+  }
+  return DKM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Index tuning
+// ---------------------------------------------------------------------------
+dkm_status tuning_check(const dkm_ctx* c, const dkm_tuning& t) {
+  const float cmax = std::max(c->opts.cells_per_centroid, kTuneMaxCpc);
+  if (!(t.cells_per_centroid > 0.f) || t.cells_per_centroid > cmax)
+    return fail(DKM_EINVAL, "cells_per_centroid must be in (0, %g] (got %g)", cmax,
+                t.cells_per_centroid);
+  if (t.tile_cut_div < kMinCutDiv || t.tile_cut_div > 1024)
+    return fail(DKM_EINVAL, "tile_cut_div must be in [%d, 1024] (got %d)", kMinCutDiv,
+                t.tile_cut_div);
+  if (t.row_filter_min < 0) return fail(DKM_EINVAL, "row_filter_min must be >= 0");
+  return DKM_OK;
+}
+
+dkm_status apply_tuning(dkm_ctx* c, const dkm_tuning& t) {
+  DKM_TRY(tuning_check(c, t));
+  bool changed = false;
+  if (t.cells_per_centroid != c->cpc) {
+    c->cpc = t.cells_per_centroid;
+    DKM_TRY(plan_clouds(c, c->h_blo, c->h_bhi));
+    DKM_TRY(upload_clouds(c));
+    changed = true;
+  }
+  if (t.tile_cut_div != c->cut_div) {
+    c->cut_div = t.tile_cut_div;
+    DKM_TRY(apply_tiling(c));
+    changed = true;
+  }
+  if (t.row_filter_min != c->row_filter_min) {
+    c->row_filter_min = t.row_filter_min;
+    changed = true;
+  }
+  if (changed) {
+    destroy_graph(c);
+    c->acc_valid = false;
+  }
+  return DKM_OK;
+}
+
+dkm_tuning current_tuning(const dkm_ctx* c) {
+  dkm_tuning t;
+  memset(&t, 0, sizeof(t));
+  t.cells_per_centroid = c->cpc;
+  t.tile_cut_div = c->cut_div;
+  t.row_filter_min = c->row_filter_min;
+  return t;
+}
+
+// Mean ms per pass of `passes` Lloyd passes from the staged centroids
+// (graph launch, no early stop), best of two timed launches after one
+// warm-up launch.
+dkm_status time_passes(dkm_ctx* c, int passes, float* ms) {
+  DKM_TRY(ensure_hist(c, passes));
+  if (!c->gexec || c->g_iters != passes || c->g_algo != c->opts.algo || c->g_early != 0 ||
+      c->g_profile != 0)
+    DKM_TRY(build_run_graph(c, passes, 0, 0));
+  DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
+  float best = INFINITY;
+  for (int r = 0; r < 2; ++r) {
+    DKM_CK(cudaEventRecord(c->ev_a, c->stream));
+    DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
+    DKM_CK(cudaEventRecord(c->ev_b, c->stream));
+    DKM_CK(cudaEventSynchronize(c->ev_b));
+    best = std::min(best, ev_ms(c->ev_a, c->ev_b));
+  }
+  DevState h;
+  DKM_TRY(read_state(c, &h));
+  DKM_TRY(check_state(h));
+  *ms = best / (float)passes;
+  return DKM_OK;
+}
+
+// workload shape -> tuning, shared by every context of the process
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, dkm_tuning> g_tune_cache;
+
+TuneKey tune_key(const dkm_ctx* c) {
+  const double mn = (double)c->n / c->B, mk = (double)c->k / c->B;
+  int bb = 0;
+  while ((1 << bb) < c->B) ++bb;
+  return TuneKey(c->d, bb, (int)std::lround(std::log2(mn)), (int)std::lround(std::log2(mk)),
+                 c->opts.algo, (int)(c->opts.mem_budget_bytes >> 20));
+}
+
+dkm_status autotune_impl(dkm_ctx* c, const float* init, int passes, int use_cache,
+                         dkm_tuning* out) {
+  DKM_TRY(check_ctx(c));
+  if (!init) return fail(DKM_EINVAL, "null init centroids");
+  if (passes < 1 || passes > 64) return fail(DKM_EINVAL, "passes must be in [1, 64] (got %d)", passes);
+  const TuneKey key = tune_key(c);
+  if (use_cache) {
+    dkm_tuning hit;
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        hit = it->second;
+        found = true;
+      }
+    }
+    if (found) {
+      DKM_TRY(apply_tuning(c, hit));
+      if (out) {
+        *out = current_tuning(c);
+        out->from_cache = 1;
+      }
+      return DKM_OK;
+    }
+  }
+  DKM_TRY(stage_centroids(c, init));
+  DKM_TRY(centroid_box(c, true));
+  dkm_tuning best = current_tuning(c);
+  float best_ms = 0.f;
+  DKM_TRY(time_passes(c, passes, &best_ms));
+  const float before_ms = best_ms;
+  int trials = 1;
+  auto trial = [&](dkm_tuning t) -> dkm_status {
+    DKM_TRY(apply_tuning(c, t));
+    float ms = 0.f;
+    DKM_TRY(time_passes(c, passes, &ms));
+    ++trials;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+    return DKM_OK;
+  };
+  for (float v : {0.5f, 1.0f, 2.0f, 4.0f}) {
+    if (v == best.cells_per_centroid) continue;
+    dkm_tuning t = best;
+    t.cells_per_centroid = v;
+    DKM_TRY(trial(t));
+  }
+  for (int v : {2, 4, 8, 16, 32}) {
+    if (v == best.tile_cut_div) continue;
+    dkm_tuning t = best;
+    t.tile_cut_div = v;
+    DKM_TRY(trial(t));
+  }
+  for (int v : {16, 32, 48, 96, 256}) {
+    if (v == best.row_filter_min) continue;
+    dkm_tuning t = best;
+    t.row_filter_min = v;
+    DKM_TRY(trial(t));
+  }
+  DKM_TRY(apply_tuning(c, best));
+  destroy_graph(c);   // the next dkm_run captures with the caller's flags
+  c->acc_valid = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (out) {
+    *out = best;
+    out->ms_per_pass = best_ms;
+    out->ms_per_pass_before = before_ms;
+    out->trials = trials;
+    out->from_cache = 0;
+  }
+  return DKM_OK;
+}
+
 }  // namespace
 
 void dkm::dkm_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
@@ -476,91 +1079,33 @@ dkm_status dkm_plan(int64_t n, int d, int k, const float* bbox_lo, const float* 
       return fail(DKM_EINVAL, "bad bounding box on axis %d", a);
   }
   dkm_options o = resolve(opts);
-  int64_t max_cells = 0;
-  DKM_TRY(plan_grid(n, d, k, bbox_lo, bbox_hi, o, out, &max_cells));
-  out->scratch_bytes = arena_plan(n, d, k, max_cells, kBucketCap).total;
+  const std::vector<int> ks(1, k);
+  std::vector<int64_t> tgt;
+  int64_t tot = 0, cap_cells = 0;
+  DKM_TRY(cell_targets(ks, o.cells_per_centroid, o.mem_budget_bytes, &tgt, &tot));
+  DKM_TRY(cell_capacity(ks, o, &cap_cells));
+  int64_t dims[3];
+  double sz;
+  grid_geometry(d, bbox_lo, bbox_hi, tgt[0], dims, &sz);
+  memset(out, 0, sizeof(*out));
+  int64_t cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    out->dims[a] = (int)dims[a];
+    out->origin[a] = a < d ? bbox_lo[a] : 0.f;
+    cells *= dims[a];
+  }
+  out->cell = (float)sz;
+  out->bucket_cap = kBucketCap;
+  out->cells = cells;
+  out->index_bytes = index_bytes_for(cells, k, kBucketCap);
+  out->scratch_bytes = arena_plan(n, d, k, 1, cap_cells, kBucketCap).total;
   return DKM_OK;
 }
 
 dkm_status dkm_setup(dkm_ctx* c, const float* points) {
   if (!c) return fail(DKM_EINVAL, "null context");
   if (!points) return fail(DKM_EINVAL, "null points");
-  c->ready = false;
-  c->acc_valid = false;
-  const float* src = points;
-  if (!is_device_ptr(points)) {
-    if (!c->pstage) DKM_CK(cudaMalloc(&c->pstage, (size_t)c->n * c->d * sizeof(float)));
-    DKM_CK(cudaMemcpyAsync(c->pstage, points, (size_t)c->n * c->d * sizeof(float),
-                           cudaMemcpyHostToDevice, c->stream));
-    src = c->pstage;
-  }
-  if (c->opts.profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
-  DKM_CK(launch_bbox(src, c->n, c->d, c->st, 0, c->d, c->stream));
-  DevState h;
-  DKM_TRY(read_state(c, &h));
-  if (h.bad) return fail(DKM_EINVAL, "points contain a non-finite or |x| > 1e18 coordinate");
-  for (int a = 0; a < 3; ++a) {
-    c->pbox_lo[a] = a < c->d ? float_of(h.pbox[a]) : 0.f;
-    c->pbox_hi[a] = a < c->d ? float_of(h.pbox[3 + a]) : 0.f;
-  }
-  int64_t max_cells = 0;
-  dkm_plan_info plan;
-  DKM_TRY(plan_grid(c->n, c->d, c->k, c->pbox_lo, c->pbox_hi, c->opts, &plan, &max_cells));
-  if (plan.cells > c->max_cells) return fail(DKM_EINTERNAL, "grid plan exceeds the arena");
-  plan.scratch_bytes = c->arena_bytes;
-  c->plan = plan;
-  Grid g{};
-  for (int a = 0; a < 3; ++a) {
-    g.g0[a] = plan.origin[a];
-    g.dims[a] = plan.dims[a];
-  }
-  g.inv_s = 1.0f / plan.cell;
-  g.cap = plan.bucket_cap;
-  g.cells = plan.cells;
-  // the grid geometry is baked into the cached graph: rebuild it only if it changed
-  if (memcmp(&g, &c->grid, sizeof(Grid)) != 0 && c->gexec) destroy_graph(c);
-  c->grid = g;
-
-  // Morton keys on a cubic lattice over the bbox
-  float emax = 0.f;
-  for (int a = 0; a < c->d; ++a) emax = std::max(emax, c->pbox_hi[a] - c->pbox_lo[a]);
-  const float qmax = c->d == 3 ? 1023.f : 32767.f;
-  const float inv = emax > 0.f ? qmax / emax : 0.f;
-  DKM_CK(launch_morton(src, c->n, c->d, c->pbox_lo, inv, c->keys[0], c->vals[0], c->stream));
-  int fin = 0;
-  DKM_CK(launch_radix_sort(c->keys, c->vals, c->n, 30, c->rs_counts, c->rs_totals, &fin,
-                           c->stream));
-  c->perm = c->vals[fin];
-  DKM_CK(launch_gather(src, c->n, c->d, c->perm, c->xs, c->ys, c->zs, c->n_pad, c->stream));
-  // Tiling level: the finest Morton level whose cubes cut the sorted order
-  // into at most n_windows / 8 pieces (so the cuts add at most 1/8 tiles).
-  DKM_CK(launch_levels(c->keys[fin], c->n, c->d, c->level_hist, c->stream));
-  unsigned long long hist[kMaxLevels + 1];
-  DKM_CK(cudaMemcpyAsync(hist, c->level_hist, sizeof(hist), cudaMemcpyDeviceToHost, c->stream));
-  DKM_CK(cudaStreamSynchronize(c->stream));
-  const int levels = c->d == 3 ? 10 : 15;
-  const unsigned long long seg_cap = (unsigned long long)std::max(1, c->n_windows / 8);
-  int level = 0;
-  unsigned long long segs = 1;
-  for (int l = 1; l <= levels; ++l) {
-    segs += hist[l];
-    if (segs > seg_cap) break;
-    level = l;
-  }
-  c->tile_level = level;
-  const int shift = c->d * (levels - level);
-  DKM_CK(launch_tiles(c->keys[fin], c->n, shift, c->n_windows, c->wcnt, c->wbase, c->n_tiles_dev,
-                      c->tiles, c->stream));
-  DKM_CK(launch_tile_boxes(c->xs, c->ys, c->zs, c->d, c->tiles, c->n_tiles_dev, c->tiles_max,
-                           c->tbox, c->stream));
-  DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
-  if (c->opts.profile) {
-    DKM_CK(cudaEventRecord(c->ev_b, c->stream));
-    DKM_CK(cudaEventSynchronize(c->ev_b));
-    c->timings.setup_ms = ev_ms(c->ev_a, c->ev_b);
-  }
-  c->ready = true;
-  return DKM_OK;
+  return setup_impl(c, points);
 }
 
 dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int k,
@@ -569,92 +1114,20 @@ dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int 
   *out = nullptr;
   DKM_TRY(validate_sizes(n, d, k));
   if (!points) return fail(DKM_EINVAL, "null points");
-  dkm_ctx* c = new dkm_ctx();
-  c->n = n;
-  c->d = d;
-  c->k = k;
-  c->opts = resolve(opts);
-  c->row_filter_min = env_int("DKM_ROW_FILTER_MIN", 48);
-  auto bail = [&](dkm_status s) {
-    dkm_destroy(c);
-    return s;
-  };
-  if (cudaGetDevice(&c->device) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(DKM_ECUDA, "no CUDA device available"));
-  }
-  if (c->opts.stream) {
-    c->stream = (cudaStream_t)c->opts.stream;
-  } else {
-    if (cudaStreamCreate(&c->stream) != cudaSuccess)
-      return bail(fail(DKM_ECUDA, "cudaStreamCreate failed"));
-    c->own_stream = true;
-  }
-  c->n_blocks = (int)((n + kBlockPts - 1) / kBlockPts);
-  c->n_windows = (int)windows_of(n);
-  c->tiles_max = (int)tiles_max_of(n);
-  c->n_pad = (int64_t)c->n_blocks * kBlockPts;
-  // arena sized for the largest grid this (k, budget) can plan
-  {
-    float lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-    dkm_plan_info p;
-    int64_t mc = 0;
-    dkm_status s = plan_grid(n, d, k, lo, hi, c->opts, &p, &mc);
-    if (s != DKM_OK) return bail(s);
-    c->max_cells = mc;
-  }
-  ArenaPlan P = arena_plan(n, d, k, c->max_cells, kBucketCap);
-  cudaError_t e = cudaMalloc(&c->arena, P.total);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    c->arena = nullptr;
-    return bail(fail(DKM_ENOMEM, "cudaMalloc(%zu B) failed: %s", P.total, cudaGetErrorString(e)));
-  }
-  c->arena_bytes = P.total;
-  c->index_bytes = index_bytes_for(c->max_cells, k, kBucketCap);
-  char* base = (char*)c->arena;
-  c->xs = (float*)(base + P.xs);
-  c->ys = (float*)(base + P.ys);
-  c->zs = d == 3 ? (float*)(base + P.zs) : nullptr;
-  c->keys[0] = (uint32_t*)(base + P.keys0);
-  c->keys[1] = (uint32_t*)(base + P.keys1);
-  c->vals[0] = (uint32_t*)(base + P.vals0);
-  c->vals[1] = (uint32_t*)(base + P.vals1);
-  c->rs_counts = (uint32_t*)(base + P.rs_counts);
-  c->rs_totals = (uint32_t*)(base + P.rs_totals);
-  c->tbox = (float4*)(base + P.tbox);
-  c->tiles = (int2*)(base + P.tiles);
-  c->n_tiles_dev = (int*)(base + P.n_tiles);
-  c->wcnt = (int*)(base + P.wcnt);
-  c->wbase = (int*)(base + P.wbase);
-  c->level_hist = (unsigned long long*)(base + P.level_hist);
-  c->lab = (int32_t*)(base + P.lab);
-  c->cw = (float4*)(base + P.cw);
-  c->acc = (Acc*)(base + P.acc);
-  c->slots = (Slot*)(base + P.slots);
-  c->st = (DevState*)(base + P.st);
-  c->gcnt[0] = (int*)(base + P.gcnt0);
-  c->gcnt[1] = (int*)(base + P.gcnt1);
-  c->gbkt[0] = (float4*)(base + P.gbkt0);
-  c->gbkt[1] = (float4*)(base + P.gbkt1);
-  c->ovf[0] = (float4*)(base + P.ovf0);
-  c->ovf[1] = (float4*)(base + P.ovf1);
-  c->ovf_cnt = (int*)(base + P.ovf_cnt);
-  c->tlist = (int*)(base + P.tlist);
-  c->tcnt = (int*)(base + P.tcnt);
-  c->cstage = (float*)(base + P.cstage);
-  c->cstage2 = (float*)(base + P.cstage2);
-  c->kstage = (int32_t*)(base + P.kstage);
-  if (cudaMemsetAsync(c->arena, 0, P.total, c->stream) != cudaSuccess ||
-      cudaEventCreate(&c->ev_a) != cudaSuccess || cudaEventCreate(&c->ev_b) != cudaSuccess ||
-      cudaEventCreate(&c->ev_c) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(DKM_ECUDA, "context initialisation failed"));
-  }
-  dkm_status s = dkm_setup(c, points);
-  if (s != DKM_OK) return bail(s);
-  *out = c;
-  return DKM_OK;
+  return create_impl(out, points, std::vector<int64_t>{0, n}, std::vector<int>{k}, d, opts);
+}
+
+dkm_status dkm_create_batched(dkm_ctx** out, const float* points, const int64_t* offsets, int B,
+                              int d, const int32_t* ks, const dkm_options* opts) {
+  if (!out) return fail(DKM_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!points || !offsets || !ks) return fail(DKM_EINVAL, "null argument");
+  if (B < 1 || B > kMaxClouds) return fail(DKM_EINVAL, "B must be in [1, %d] (got %d)", kMaxClouds, B);
+  std::vector<int64_t> off;
+  std::vector<int32_t> kv;
+  DKM_TRY(host_copy(offsets, (size_t)B + 1, &off));
+  DKM_TRY(host_copy(ks, (size_t)B, &kv));
+  return create_impl(out, points, off, std::vector<int>(kv.begin(), kv.end()), d, opts);
 }
 
 dkm_status dkm_assign(dkm_ctx* c, const float* centroids, int32_t* labels, double* sse_out,
@@ -716,59 +1189,28 @@ dkm_status dkm_update(dkm_ctx* c, const int32_t* labels, float* centroids_inout,
 
 dkm_status dkm_run(dkm_ctx* c, const float* init, int max_iter, float* centroids_out,
                    int32_t* labels_out, int* iterations_out, double* sse_out) {
-  DKM_TRY(check_ctx(c));
-  if (!init) return fail(DKM_EINVAL, "null init centroids");
-  if (max_iter < 0 || max_iter > kMaxIterCap)
-    return fail(DKM_EINVAL, "max_iter must be in [0, %d] (got %d)", kMaxIterCap, max_iter);
-  c->acc_valid = false;
-  DKM_TRY(stage_centroids(c, init));
-  DKM_TRY(centroid_box(c, true));
   DevState h;
-  if (max_iter == 0) {
-    DKM_TRY(one_pass(c, false));
-    DKM_TRY(export_labels(c, labels_out, false));
-    DKM_TRY(export_centroids(c, centroids_out));
-    DKM_TRY(read_state(c, &h));
-    DKM_TRY(check_state(h));
-    if (iterations_out) *iterations_out = 0;
-    if (sse_out) *sse_out = h.last_sse;
-    return DKM_OK;
+  DKM_TRY(run_impl(c, init, max_iter, centroids_out, labels_out, &h));
+  if (iterations_out) *iterations_out = max_iter == 0 ? 0 : h.passes;
+  if (sse_out) *sse_out = max_iter == 0 ? h.last_sse : h.final_sse;
+  return DKM_OK;
+}
+
+dkm_status dkm_run_batched(dkm_ctx* c, const float* init, int max_iter, float* centroids_out,
+                           int32_t* labels_out, int32_t* iterations_out, double* sse_out) {
+  DevState h;
+  DKM_TRY(run_impl(c, init, max_iter, centroids_out, labels_out, &h));
+  if (!iterations_out && !sse_out) return DKM_OK;
+  std::vector<CloudRun> hr;
+  DKM_TRY(read_clouds(c, &hr));
+  std::vector<int32_t> it(c->B);
+  std::vector<double> ss(c->B);
+  for (int b = 0; b < c->B; ++b) {
+    it[b] = max_iter == 0 ? 0 : hr[b].passes;
+    ss[b] = max_iter == 0 ? hr[b].last_sse : hr[b].final_sse;
   }
-  DKM_TRY(ensure_hist(c, max_iter));
-  const int early = c->opts.early_stop ? 1 : 0;
-  const int profile = c->opts.profile ? 1 : 0;
-  if (!c->gexec || c->g_iters != max_iter || c->g_algo != c->opts.algo || c->g_early != early ||
-      c->g_profile != profile)
-    DKM_TRY(build_run_graph(c, max_iter, early, profile));
-  if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
-  DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
-  if (profile) DKM_CK(cudaEventRecord(c->ev_b, c->stream));
-  // final labels in caller order + SSE of those labels against the final centroids
-  IterArgs A = iter_args(c, 0, 0);
-  DKM_TRY(export_labels(c, labels_out, true));
-  DKM_CK(launch_collect(A, -2, c->stream));
-  DKM_TRY(export_centroids(c, centroids_out));
-  if (profile) DKM_CK(cudaEventRecord(c->ev_c, c->stream));
-  DKM_TRY(read_state(c, &h));
-  DKM_TRY(check_state(h));
-  if (iterations_out) *iterations_out = h.passes;
-  if (sse_out) *sse_out = h.final_sse;
-  if (profile) {
-    dkm_timings& T = c->timings;
-    T.iterations_ms = ev_ms(c->ev_a, c->ev_b);
-    T.finalize_ms = ev_ms(c->ev_b, c->ev_c);
-    T.passes = h.passes;
-    double s = 0, a = 0, u = 0;
-    for (int t = 0; t < h.passes && t < max_iter; ++t) {
-      s += ev_ms(c->ev[4 * t + 0], c->ev[4 * t + 1]);
-      a += ev_ms(c->ev[4 * t + 1], c->ev[4 * t + 2]);
-      u += ev_ms(c->ev[4 * t + 2], c->ev[4 * t + 3]);
-    }
-    int p = h.passes > 0 ? h.passes : 1;
-    T.search_ms = (float)(s / p);
-    T.assign_ms = (float)(a / p);
-    T.update_ms = (float)(u / p);
-  }
+  DKM_TRY(put_small(iterations_out, it.data(), it.size()));
+  DKM_TRY(put_small(sse_out, ss.data(), ss.size()));
   return DKM_OK;
 }
 
@@ -782,6 +1224,37 @@ dkm_status dkm_fit(const float* points, int64_t n, int d, int k, const float* in
   dkm_destroy(c);
   g_last_error = keep;
   return s;
+}
+
+dkm_status dkm_fit_batched(const float* points, const int64_t* offsets, int B, int d,
+                           const int32_t* ks, const float* init, int max_iter,
+                           float* centroids_out, int32_t* labels_out, int32_t* iterations_out,
+                           double* sse_out, const dkm_options* opts) {
+  dkm_ctx* c = nullptr;
+  DKM_TRY(dkm_create_batched(&c, points, offsets, B, d, ks, opts));
+  dkm_status s =
+      dkm_run_batched(c, init, max_iter, centroids_out, labels_out, iterations_out, sse_out);
+  std::string keep = g_last_error;
+  dkm_destroy(c);
+  g_last_error = keep;
+  return s;
+}
+
+dkm_status dkm_get_tuning(const dkm_ctx* c, dkm_tuning* out) {
+  if (!c || !out) return fail(DKM_EINVAL, "null argument");
+  *out = current_tuning(c);
+  return DKM_OK;
+}
+
+dkm_status dkm_set_tuning(dkm_ctx* c, const dkm_tuning* t) {
+  DKM_TRY(check_ctx(c));
+  if (!t) return fail(DKM_EINVAL, "null tuning");
+  return apply_tuning(c, *t);
+}
+
+dkm_status dkm_autotune(dkm_ctx* c, const float* init, int passes, int use_cache,
+                        dkm_tuning* out) {
+  return autotune_impl(c, init, passes, use_cache, out);
 }
 
 dkm_status dkm_query_memory(const dkm_ctx* c, size_t* device_bytes, size_t* index_bytes) {
@@ -812,7 +1285,7 @@ dkm_status dkm_last_stats(dkm_ctx* c, dkm_stats* out) {
   DKM_TRY(read_state(c, &h));
   out->evals_per_point = (double)h.last_evals / (double)c->n;
   out->candidates_per_tile = h.last_tiles ? (double)h.last_cands / (double)h.last_tiles : 0.0;
-  out->tiles = (int64_t)h.last_tiles;
+  out->tiles = (int64_t)c->n_tiles;
   out->tile_level = c->tile_level;
   out->fallback_tiles = (int64_t)h.last_fallback;
   out->grid_overflow = (int64_t)h.grid_ovf;

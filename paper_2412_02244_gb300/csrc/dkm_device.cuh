@@ -34,40 +34,40 @@ constexpr int kMaxLevels = 16;     // Morton levels (10 in 3D, 15 in 2D) + "neve
 // about 5 ulp relative); 1 + 2^-16 leaves a 12x margin.
 constexpr float kKeep = 1.0000152587890625f;
 
-// Per-slot counters, 64 bytes so two slots never share a 32-byte sector.
+// Per-slot pruning counters, 64 bytes so two slots never share a 32-byte
+// sector.
 struct Slot {
-  unsigned long long sse;       // fixed point, unit 2^-s_sse
-  unsigned long long changed;   // labels that differ from the previous pass
   unsigned long long evals;     // point x candidate distance evaluations
-  unsigned long long cands;     // sum of block candidate-list lengths
-  unsigned long long fallback;  // blocks whose candidate list overflowed
-  unsigned long long pad[3];
+  unsigned long long cands;     // sum of tile candidate-list lengths
+  unsigned long long fallback;  // tiles whose candidate list overflowed
+  unsigned long long pad[5];
 };
 
-// Device-resident run state.
+// Device-resident run state (whole context).
 struct DevState {
-  unsigned pbox[6];      // ordered-uint point bbox: lo[3], hi[3]
-  unsigned cbox[6];      // ordered-uint centroid bbox of the current run
+  unsigned pbox[6];      // ordered-uint bbox (used by the allocation-free step)
+  unsigned cbox[6];
   int bad;               // non-finite or out-of-range coordinate seen
-  int done;              // early stop reached
-  int passes;            // assignment passes executed in the current run
+  int n_done;            // clouds that reached their early stop
+  int passes;            // max over clouds of the passes of the current run
   int err;               // internal error bits (kErr*)
-  int label_err;         // dkm_update: a label outside [0, k)
+  int label_err;         // dkm_update: a label outside [0, k_b)
   int pad0;
   unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles;
-  unsigned long long grid_ovf;   // centroids put in the overflow list, last rebuild
-  double last_sse;               // SSE of the last pass (against its input centroids)
-  double final_sse;              // SSE of the final labels against the final centroids
+  unsigned long long grid_ovf;   // centroids put in an overflow list, last rebuild
+  double last_sse;               // total SSE of the last pass (against its input centroids)
+  double final_sse;              // total SSE of the final labels against the final centroids
 };
 
 constexpr int kErrEmptyList = 1;     // a tile found no candidate (cannot happen for k >= 1)
 constexpr int kErrNoCentroid = 2;    // the search found no centroid at all
 
 // Accumulator per centroid: sum of residuals (p - c_old) per axis in fixed
-// point (two's complement in u64, unit 2^-s_glob) and the count.
+// point (two's complement in u64, unit 2^-s_glob of its cloud) and the count.
 struct Acc { unsigned long long s[3]; unsigned long long cnt; };
 
-// Centroid grid geometry (uniform cells; border cells are open-ended).
+// Centroid grid geometry of one cloud (uniform cells; border cells are
+// open-ended).
 struct Grid {
   float g0[3];
   float inv_s;
@@ -76,27 +76,68 @@ struct Grid {
   long long cells;
 };
 
+// One point cloud of a context (a context holds B >= 1 independent
+// k-means problems).  Points of cloud b occupy sorted positions
+// [p0, p0 + n) -- the same range as in the caller's concatenated input,
+// because the cloud index is the most significant part of the sort key --
+// and its centroids are [c0, c0 + k) of the context's centroid arrays.
+struct Cloud {
+  int64_t p0, n;
+  int c0, k;
+  long long cell0;       // first cell of its grid in the shared cell arrays
+  Grid grid;
+  float mlo[3];          // Morton lattice: origin and 1 / step
+  float minv;
+  int shift;             // tiles are cut where (key >> shift) changes
+  int t0;                // its first tile
+};
+
+// Per-cloud run state.
+struct CloudRun {
+  unsigned pbox[6];      // ordered-uint point bbox: lo[3], hi[3]
+  unsigned cbox[6];      // ordered-uint bbox of the run's initial centroids
+  int s_glob, s_sse;     // fixed-point exponents of the run (fixed_exponents)
+  int done;              // early stop reached
+  int passes;            // assignment passes executed in the current run
+  unsigned long long last_changed;
+  double last_sse;
+  double final_sse;
+};
+
+// Per-cloud pass counters, spread over kCloudSlots addresses.
+constexpr int kCloudSlots = 8;
+struct CloudAcc {
+  unsigned long long sse[kCloudSlots];      // fixed point, unit 2^-s_sse of the cloud
+  unsigned long long changed[kCloudSlots];
+};
+
 // Everything an iteration kernel needs (passed by value).
 struct IterArgs {
-  int64_t n;
-  int k;
+  int64_t n;                 // total points
+  int k;                     // total centroids
+  int B;                     // clouds
   int n_windows;             // ceil(n / 256)
-  int tiles_max;             // launch bound on the tile count
-  const int* n_tiles;        // actual tile count (device)
+  int n_tiles;               // tiles of the point index (launch size)
   const int2* tiles;         // per tile: [start, end) in sorted order
+  const int* tcloud;         // per tile: its cloud
+  const int* kcloud;         // per centroid: its cloud
+  const Cloud* clouds;
+  Cloud cl0;                 // copy of clouds[0] (kernel-parameter space)
+  CloudRun* crun;
+  CloudAcc* cacc;
   const float* xs; const float* ys; const float* zs;   // sorted SoA points
   const float4* tbox;        // per tile: lo, hi (2 x float4)
-  int32_t* lab;              // sorted labels
+  int32_t* lab;              // sorted labels (context-wide centroid index)
   float4* cw;                // working centroids (x, y, z, id bits)
   Acc* acc;                  // per centroid
   Slot* slots;
   DevState* st;
-  Grid grid;
+  long long total_cells;     // cells of all clouds' grids
   int* gcnt[2];              // per cell fill counter, two parities
   float4* gbkt[2];           // cells * cap entries
-  float4* ovf[2];            // overflow list (k entries)
-  int* ovf_cnt;              // [2]
-  int* tlist;                // tiles_max * kTileCap candidate ids (unordered)
+  float4* ovf[2];            // overflow lists: cloud b uses [c0, c0 + k)
+  int* ovf_cnt[2];           // per cloud overflow count, two parities
+  int* tlist;                // n_tiles * kTileCap candidate ids (unordered)
   int* tcnt;                 // per tile list length (> kTileCap = overflow)
   double* sse_hist;
   unsigned long long* chg_hist;
@@ -153,13 +194,16 @@ __device__ __forceinline__ long long rescale(long long v, int s_from, int s_to) 
 //   s_glob: unit 2^-s_glob for per-centroid residual sums, so that
 //           n * (2 * extent) * 2^s_glob <= 2^62;
 //   s_sse : unit for the SSE, so that n * 4 * extent^2 * 2^s_sse <= 2^62.
-__device__ __forceinline__ void fixed_exponents(const DevState* st, int64_t n, int* s_glob,
-                                                int* s_sse) {
+// extent = the largest axis extent of the union of the point and the
+// initial-centroid boxes (every later centroid is a mean of points, so it
+// stays inside).
+__device__ __forceinline__ void fixed_exponents_box(const unsigned* pbox, const unsigned* cbox,
+                                                    int64_t n, int* s_glob, int* s_sse) {
   float E = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float lo = fminf(float_of(st->pbox[a]), float_of(st->cbox[a]));
-    float hi = fmaxf(float_of(st->pbox[3 + a]), float_of(st->cbox[3 + a]));
+    float lo = fminf(float_of(pbox[a]), float_of(cbox[a]));
+    float hi = fmaxf(float_of(pbox[3 + a]), float_of(cbox[3 + a]));
     float e = hi - lo;
     E = fmaxf(E, e == e ? e : 0.f);
   }
@@ -167,6 +211,11 @@ __device__ __forceinline__ void fixed_exponents(const DevState* st, int64_t n, i
   int en = 64 - __clzll((unsigned long long)n);  // n < 2^en
   *s_glob = 62 - en - eE;
   *s_sse = 60 - en - 2 * eE;
+}
+
+__device__ __forceinline__ void fixed_exponents(const DevState* st, int64_t n, int* s_glob,
+                                                int* s_sse) {
+  fixed_exponents_box(st->pbox, st->cbox, n, s_glob, s_sse);
 }
 
 __device__ __forceinline__ float mind2(const float4& lo, const float4& hi, float cx, float cy,

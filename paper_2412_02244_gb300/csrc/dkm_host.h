@@ -13,25 +13,28 @@
 namespace dkm {
 
 // dkm_setup.cu
-cudaError_t launch_bbox(const float* p, int64_t n, int d, DevState* st, int which, int d_ctx,
-                        cudaStream_t s);
-cudaError_t launch_morton(const float* p, int64_t n, int d, const float* lo, float inv,
-                          uint32_t* keys, uint32_t* vals, cudaStream_t s);
+cudaError_t launch_bbox(const float* p, int d, const int64_t* seg, int B, int64_t max_rows,
+                        CloudRun* crun, DevState* st, int which, int d_ctx, cudaStream_t s);
+cudaError_t launch_exponents(const Cloud* clouds, CloudRun* crun, int B, cudaStream_t s);
+cudaError_t launch_morton(const float* p, int64_t n, int d, const int64_t* seg, int B,
+                          const Cloud* clouds, int mb, uint32_t* keys, uint32_t* vals,
+                          cudaStream_t s);
 int64_t radix_sort_nb(int64_t n);
 cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits,
                               uint32_t* counts, uint32_t* totals, int* final_buf, cudaStream_t s);
 cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,
                           float* ys, float* zs, int64_t n_pad, cudaStream_t s);
-cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, unsigned long long* hist,
-                          cudaStream_t s);
-cudaError_t launch_tiles(const uint32_t* keys, int64_t n, int shift, int n_windows, int* wcnt,
-                         int* wbase, int* n_tiles, int2* tiles, cudaStream_t s);
+cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,
+                          unsigned long long* hist, cudaStream_t s);
+cudaError_t launch_tiles(const uint32_t* keys, int64_t n, const Cloud* clouds, int d, int mb,
+                         int B, int n_windows, int* wcnt, int* wbase, int* n_tiles, int2* tiles,
+                         cudaStream_t s);
 cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
-                              const int2* tiles, const int* n_tiles, int tiles_max, float4* tbox,
-                              cudaStream_t s);
+                              const int2* tiles, int n_tiles, const uint32_t* keys, int mb, int B,
+                              float4* tbox, int* tcloud, Cloud* clouds, cudaStream_t s);
 
 // dkm_iter.cu
-cudaError_t launch_reset_run(DevState* st, cudaStream_t s);
+cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s);
 cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const float* user_c,
                              int insert, int par, int32_t* counts_out, cudaStream_t s);
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s);
@@ -48,22 +51,37 @@ void dkm_set_last_error(const char* msg);
 
 }  // namespace dkm
 
+// A context holds B >= 1 independent k-means problems ("clouds") over one
+// concatenated point array; the single-cloud API is the case B = 1.
 struct dkm_ctx {
-  int64_t n = 0;
-  int d = 0, k = 0;
+  int64_t n = 0;               // total points
+  int d = 0;
+  int k = 0;                   // total centroids (sum of ks)
+  int B = 1;                   // clouds
+  std::vector<int64_t> offsets;   // B + 1 point offsets
+  std::vector<int> ks;            // B centroid counts
+  std::vector<int64_t> coffs;     // B + 1 centroid offsets
+  int64_t max_n_b = 0, max_k_b = 0;
+  int mb = 10;                 // Morton bits per axis
+  int key_bits = 30;           // significant bits of the sort key
   dkm_options opts{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
   int n_blocks = 0;            // 2048-point padding blocks
   int n_windows = 0;           // 256-point windows
-  int tiles_max = 0;           // capacity of the tile arrays
-  int tile_level = 0;          // Morton level whose cube boundaries cut tiles
+  int tiles_cap = 0;           // capacity of the tile arrays
+  int n_tiles = 0;             // tiles of the current point index
+  int tile_level = 0;          // Morton level whose cube boundaries cut cloud 0's tiles
+  int cut_div = 8;             // cube cuts may add n_windows / cut_div tiles per cloud
+  float cpc = 1.0f;            // grid cells per centroid (before the budget cap)
   int64_t n_pad = 0;
   int64_t max_cells = 0;       // grid capacity the arena was sized for
+  int64_t total_cells = 0;     // cells of the current grids
   dkm_plan_info plan{};
-  dkm::Grid grid{};
-  float pbox_lo[3] = {0, 0, 0}, pbox_hi[3] = {0, 0, 0};
+  std::vector<dkm::Cloud> h_clouds;               // host copy of the cloud table
+  std::vector<unsigned long long> h_level_hist;   // B x (kMaxLevels + 1)
+  std::vector<float> h_blo, h_bhi;                // per-cloud point boxes (3 floats each)
   int row_filter_min = 48;     // per-row candidate filtering threshold
   bool ready = false;          // the point index is valid
   bool acc_valid = false;      // acc holds the sums of the last dkm_assign
@@ -71,17 +89,23 @@ struct dkm_ctx {
   // device arena
   void* arena = nullptr;
   size_t arena_bytes = 0;
-  size_t index_bytes = 0;
   float *xs = nullptr, *ys = nullptr, *zs = nullptr;
   uint32_t* keys[2] = {nullptr, nullptr};
   uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* skeys = nullptr;   // sorted keys (one of keys[])
   uint32_t* perm = nullptr;    // sorted position -> original index
   uint32_t *rs_counts = nullptr, *rs_totals = nullptr;
   float4* tbox = nullptr;
   int2* tiles = nullptr;
   int* n_tiles_dev = nullptr;
+  int* tcloud = nullptr;
+  int* kcloud = nullptr;
   int *wcnt = nullptr, *wbase = nullptr;
   unsigned long long* level_hist = nullptr;
+  int64_t *doff = nullptr, *dcoff = nullptr;
+  dkm::Cloud* clouds = nullptr;
+  dkm::CloudRun* crun = nullptr;
+  dkm::CloudAcc* cacc = nullptr;
   int32_t* lab = nullptr;
   float4* cw = nullptr;
   dkm::Acc* acc = nullptr;
@@ -90,7 +114,7 @@ struct dkm_ctx {
   int* gcnt[2] = {nullptr, nullptr};
   float4* gbkt[2] = {nullptr, nullptr};
   float4* ovf[2] = {nullptr, nullptr};
-  int* ovf_cnt = nullptr;
+  int* ovf_cnt[2] = {nullptr, nullptr};
   int* tlist = nullptr;
   int* tcnt = nullptr;
   float* cstage = nullptr;     // k x d centroid staging

@@ -37,79 +37,132 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long
   atomicAdd(p, v);
 }
 
-// Reduce the spread slots into the run history / last-pass counters and
-// clear them.  Called by one full CTA of kBlockThreads threads.
-//   t >= 0: pass t of a run (history + early-stop flag)
+// Fold the counters of a pass, per cloud (SSE, changed labels, early stop
+// -> CloudRun) and in total (run history, last-pass statistics), and clear
+// them.  Called by one full CTA of kBlockThreads threads.
+//   t >= 0: pass t of a run (only clouds that executed it)
 //   t == -1: a single pass outside a run
-//   t == -2: the final-SSE pass of a run (only final_sse is written)
-__device__ void collect_slots(const IterArgs& A, int t) {
+//   t == -2: the final-SSE pass of a run (only the final SSEs are written)
+// Sums over clouds run in a fixed order, so the totals are deterministic.
+__device__ void collect_pass(const IterArgs& A, int t) {
+  __shared__ double s_sse[kBlockThreads / 32];
   __shared__ unsigned long long s_part[5][kBlockThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long v[5] = {0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
-    Slot& s = A.slots[i];
-    v[0] += s.sse; v[1] += s.changed; v[2] += s.evals; v[3] += s.cands; v[4] += s.fallback;
-    s.sse = 0; s.changed = 0; s.evals = 0; s.cands = 0; s.fallback = 0;
+  double sse = 0.0;
+  unsigned long long v[5] = {0, 0, 0, 0, 0};   // changed, evals, cands, fallback, clouds run
+  for (int b = threadIdx.x; b < A.B; b += blockDim.x) {
+    CloudRun& r = A.crun[b];
+    if (t >= 0 && r.passes != t + 1) continue;   // the cloud stopped earlier
+    CloudAcc& a = A.cacc[b];
+    unsigned long long qs = 0, qc = 0;
+#pragma unroll
+    for (int q = 0; q < kCloudSlots; ++q) {
+      qs += a.sse[q];
+      qc += a.changed[q];
+      a.sse[q] = 0;
+      a.changed[q] = 0;
+    }
+    const double e = (double)(long long)qs * exp2(-(double)r.s_sse);
+    sse += e;
+    if (t == -2) {
+      r.final_sse = e;
+      continue;
+    }
+    r.last_sse = e;
+    r.last_changed = qc;
+    v[0] += qc;
+    v[4] += 1;
+    if (t >= 0 && A.early_stop && qc == 0) {
+      r.done = 1;
+      atomicAdd(&A.st->n_done, 1);
+    }
   }
+  if (t != -2) {
+    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+      Slot& s = A.slots[i];
+      v[1] += s.evals; v[2] += s.cands; v[3] += s.fallback;
+      s.evals = 0; s.cands = 0; s.fallback = 0;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, o);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     if (lane == 0) s_part[q][w] = v[q];
   }
+  if (lane == 0) s_sse[w] = sse;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long tot[5] = {0, 0, 0, 0, 0};
-    for (int q = 0; q < 5; ++q)
-      for (int ww = 0; ww < (int)(blockDim.x / 32); ++ww) tot[q] += s_part[q][ww];
-    int s_glob, s_sse;
-    fixed_exponents(A.st, A.n, &s_glob, &s_sse);
-    double sse = (double)(long long)tot[0] * exp2(-(double)s_sse);
-    if (t == -2) {   // final SSE of a run: leave the last-pass counters alone
-      A.st->final_sse = sse;
-      return;
+    double tsse = 0.0;
+    for (int ww = 0; ww < (int)(blockDim.x / 32); ++ww) {
+      tsse += s_sse[ww];
+      for (int q = 0; q < 5; ++q) tot[q] += s_part[q][ww];
     }
-    A.st->last_sse = sse;
-    A.st->last_changed = tot[1];
-    A.st->last_evals = tot[2];
-    A.st->last_cands = tot[3];
-    A.st->last_fallback = tot[4];
-    A.st->last_tiles = (unsigned long long)(*A.n_tiles);
-    if (t >= 0) {
-      A.sse_hist[t] = sse;
-      A.chg_hist[t] = tot[1];
-      if (A.early_stop && tot[1] == 0) A.st->done = 1;
+    if (t == -2) {   // final SSE of a run: leave the last-pass counters alone
+      A.st->final_sse = tsse;
+    } else {
+      A.st->last_sse = tsse;
+      A.st->last_changed = tot[0];
+      A.st->last_evals = tot[1];
+      A.st->last_cands = tot[2];
+      A.st->last_fallback = tot[3];
+      A.st->last_tiles = (unsigned long long)A.n_tiles;
+      if (t >= 0 && tot[4] > 0) {
+        A.sse_hist[t] = tsse;
+        A.chg_hist[t] = tot[0];
+        A.st->passes = t + 1;
+      }
     }
   }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kBlockThreads) k_collect(IterArgs A, int t) {
-  collect_slots(A, t);
+  collect_pass(A, t);
 }
 
-__global__ void k_reset_run(DevState* st) {
-  st->done = 0;
-  st->passes = 0;
-  st->err = 0;
-  st->label_err = 0;
-  st->grid_ovf = 0;
+// clear the run state of the context and of every cloud
+__global__ void k_reset_run(DevState* st, CloudRun* crun, CloudAcc* cacc, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) {
+    st->n_done = 0;
+    st->passes = 0;
+    st->err = 0;
+    st->label_err = 0;
+    st->grid_ovf = 0;
+  }
+  if (b >= B) return;
+  crun[b].done = 0;
+  crun[b].passes = 0;
+  crun[b].last_changed = 0;
+  crun[b].last_sse = 0.0;
+  crun[b].final_sse = 0.0;
+  for (int q = 0; q < kCloudSlots; ++q) {
+    cacc[b].sse[q] = 0;
+    cacc[b].changed[q] = 0;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // k_centroids: prep (copy user centroids in) or update (refine), then
-// optionally insert every centroid into grid parity `par`.
+// optionally insert every centroid into its cloud's grid of parity `par`.
 //   mode 0: cw[j] = user_c[j]
 //   mode 1: cw[j] += acc mean residual (if the cluster is non-empty); acc cleared
-// With t >= 0 (inside a run) an update only happens if pass t ran, and
-// CTA 0 first folds the pass's slot counters into the history.
+// With t >= 0 (inside a run) a cloud's centroids are only updated if the
+// cloud executed pass t, and CTA 0 first folds the pass's counters.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mode, int t, int d,
                                                              const float* __restrict__ user_c,
                                                              int insert, int par,
                                                              int32_t* __restrict__ counts_out) {
-  if (mode == 1 && t >= 0 && A.st->passes != t + 1) return;   // stopped early
-  if (mode == 1 && t >= 0 && blockIdx.x == 0) collect_slots(A, t);
+  // (no kernel-wide early exit: n_done changes inside this kernel, so only
+  // the per-cloud pass counts, fixed since k_assign, decide what runs)
+  if (mode == 1 && t >= 0 && blockIdx.x == 0) collect_pass(A, t);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= A.k) return;
+  const int b = A.kcloud[j];
+  if (mode == 1 && t >= 0 && A.crun[b].passes != t + 1) return;   // stopped earlier
   float4 c;
   if (mode == 0) {
     c.x = user_c[(int64_t)j * d + 0];
@@ -123,9 +176,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
     long long cnt = (long long)a.cnt;
     if (counts_out) counts_out[j] = (int32_t)cnt;
     if (cnt > 0) {
-      int s_glob, s_sse;
-      fixed_exponents(A.st, A.n, &s_glob, &s_sse);
-      const double u = exp2(-(double)s_glob) / (double)cnt;
+      const double u = exp2(-(double)A.crun[b].s_glob) / (double)cnt;
       c.x = (float)((double)c.x + (double)(long long)a.s[0] * u);
       c.y = (float)((double)c.y + (double)(long long)a.s[1] * u);
       if (d == 3) c.z = (float)((double)c.z + (double)(long long)a.s[2] * u);
@@ -133,17 +184,18 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
   }
   A.cw[j] = c;
   if (insert) {
-    const Grid& G = A.grid;
+    const Cloud& cl = A.clouds[b];
+    const Grid& G = cl.grid;
     int cx = cell_coord(c.x, G.g0[0], G.inv_s, G.dims[0]);
     int cy = cell_coord(c.y, G.g0[1], G.inv_s, G.dims[1]);
     int cz = d == 3 ? cell_coord(c.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
-    long long cell = ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
+    long long cell = cl.cell0 + ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
     int slot = atomicAdd(&A.gcnt[par][cell], 1);
     if (slot < kBucketCap) {
       A.gbkt[par][cell * kBucketCap + slot] = c;
     } else {
-      int o = atomicAdd(&A.ovf_cnt[par], 1);
-      A.ovf[par][o] = c;
+      int o = atomicAdd(&A.ovf_cnt[par][b], 1);
+      A.ovf[par][cl.c0 + o] = c;
       atomicAdd(&A.st->grid_ovf, 1ull);
     }
   }
@@ -181,28 +233,36 @@ __device__ __forceinline__ void decode_cell(long long q, int nx, int ny, int& dx
   dz = (int)z;
 }
 
-__global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(IterArgs A, int par, int d) {
-  if (A.early_stop && A.st->done) return;
-  // clear the other parity's grid for the next rebuild (nobody reads it now)
+// MULTI = false: a single cloud, whose table entry is read from the kernel
+// parameters (constant bank) instead of global memory.
+template <bool MULTI>
+__global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_constant__ IterArgs A,
+                                                                  int par, int d) {
+  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
+  // clear the other parity's grids for the next rebuild (nobody reads them now)
   {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c = g; c < A.grid.cells; c += stride) A.gcnt[par ^ 1][c] = 0;
-    if (g == 0) A.ovf_cnt[par ^ 1] = 0;
+    for (long long c = g; c < A.total_cells; c += stride) A.gcnt[par ^ 1][c] = 0;
+    for (long long c = g; c < A.B; c += stride) A.ovf_cnt[par ^ 1][c] = 0;
   }
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int t = blockIdx.x * kSearchWarps + wl;
-  if (t >= A.tiles_max || t >= *A.n_tiles) return;
+  if (t >= A.n_tiles) return;
+  const int b = MULTI ? A.tcloud[t] : 0;
+  if (MULTI && A.crun[b].done) return;
   int* __restrict__ out = A.tlist + (int64_t)t * kTileCap;
-  const Grid G = A.grid;
+  const Cloud& cl = MULTI ? A.clouds[b] : A.cl0;
+  const Grid G = cl.grid;
+  const int c0 = cl.c0, c1 = cl.c0 + cl.k;
   const float4 lo = A.tbox[2 * t], hi = A.tbox[2 * t + 1];
-  const int* __restrict__ gcnt = A.gcnt[par];
-  const float4* __restrict__ gbkt = A.gbkt[par];
-  const int n_ovf = A.ovf_cnt[par];
-  const float4* __restrict__ ovf = A.ovf[par];
+  const int* __restrict__ gcnt = A.gcnt[par] + cl.cell0;
+  const float4* __restrict__ gbkt = A.gbkt[par] + cl.cell0 * kBucketCap;
+  const int n_ovf = A.ovf_cnt[par][b];
+  const float4* __restrict__ ovf = A.ovf[par] + c0;
   // a range of more than k / 4 cells costs more than reading every centroid
-  // once, so large ranges scan the flat centroid array instead
-  const long long flat_cells = (long long)(A.k / 4) + 32;
+  // of the cloud once, so large ranges scan the flat centroid array instead
+  const long long flat_cells = (long long)(cl.k / 4) + 32;
 
   int clo[3], chi[3];
   clo[0] = cell_coord(lo.x, G.g0[0], G.inv_s, G.dims[0]);
@@ -226,7 +286,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(IterArgs A, in
     }
     float m = INFINITY;
     if (ncell > flat_cells) {
-      for (int j = lane; j < A.k; j += 32) {
+      for (int j = c0 + lane; j < c1; j += 32) {
         const float4 c = A.cw[j];
         m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
       }
@@ -279,12 +339,12 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(IterArgs A, in
   const unsigned lt = (1u << lane) - 1u;
   int count = 0;
   if (ncell > flat_cells) {
-    // every centroid once; the overflow list is then redundant
-    for (int j0 = 0; j0 < A.k; j0 += 32) {
+    // every centroid of the cloud once; the overflow list is then redundant
+    for (int j0 = c0; j0 < c1; j0 += 32) {
       const int j = j0 + lane;
       float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
       bool keep = false;
-      if (j < A.k) {
+      if (j < c1) {
         c = A.cw[j];
         keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k;
       }
@@ -468,59 +528,6 @@ __device__ __forceinline__ int filter_box(const float4* __restrict__ s_c, int m,
   return cnt;
 }
 
-// Row epilogue shared by k_assign and k_accum_labels: per-row fixed-point
-// residual sums grouped by label, added to the per-centroid accumulators.
-// la/lb are the labels of the lane's two points (valid flags va/vb).
-__device__ __forceinline__ void accumulate_row(const IterArgs& A, int D, float2 px, float2 py,
-                                               float2 pz, int la, int lb, bool va, bool vb,
-                                               int s_glob) {
-  float rxa = 0.f, rya = 0.f, rza = 0.f, rxb = 0.f, ryb = 0.f, rzb = 0.f;
-  if (va) {
-    float4 c = __ldg(&A.cw[la]);
-    rxa = __fadd_rn(px.x, -c.x); rya = __fadd_rn(py.x, -c.y);
-    if (D == 3) rza = __fadd_rn(pz.x, -c.z);
-  }
-  if (vb) {
-    float4 c = __ldg(&A.cw[lb]);
-    rxb = __fadd_rn(px.y, -c.x); ryb = __fadd_rn(py.y, -c.y);
-    if (D == 3) rzb = __fadd_rn(pz.y, -c.z);
-  }
-  float ml = fmaxf(fmaxf(fmaxf(fabsf(rxa), fabsf(rya)), fabsf(rza)),
-                   fmaxf(fmaxf(fabsf(rxb), fabsf(ryb)), fabsf(rzb)));
-  float m = warp_max_nonneg(ml);
-  // unit 2^-s_row with 64 * max|r| * 2^s_row < 2^30: int32 warp sums cannot overflow
-  int s_row = m > 0.f ? min(24 - exp_bound(m), 127) : 0;
-  float sc = pow2f(s_row);
-  int qxa = __float2int_rn(rxa * sc), qya = __float2int_rn(rya * sc), qza = __float2int_rn(rza * sc);
-  int qxb = __float2int_rn(rxb * sc), qyb = __float2int_rn(ryb * sc), qzb = __float2int_rn(rzb * sc);
-  bool pa = va, pb = vb;
-  const int lane = threadIdx.x & 31;
-  while (true) {
-    unsigned ma = __ballot_sync(0xffffffffu, pa);
-    unsigned mb = __ballot_sync(0xffffffffu, pb);
-    if (!(ma | mb)) break;
-    int L = ma ? __shfl_sync(0xffffffffu, la, __ffs(ma) - 1)
-               : __shfl_sync(0xffffffffu, lb, __ffs(mb) - 1);
-    bool ga = pa && la == L, gb = pb && lb == L;
-    int vx = (ga ? qxa : 0) + (gb ? qxb : 0);
-    int vy = (ga ? qya : 0) + (gb ? qyb : 0);
-    int vz = (ga ? qza : 0) + (gb ? qzb : 0);
-    int cnt = __popc(__ballot_sync(0xffffffffu, ga)) + __popc(__ballot_sync(0xffffffffu, gb));
-    int sx = __reduce_add_sync(0xffffffffu, vx);
-    int sy = __reduce_add_sync(0xffffffffu, vy);
-    int sz = D == 3 ? __reduce_add_sync(0xffffffffu, vz) : 0;
-    if (lane == 0) {
-      Acc* a = &A.acc[L];
-      red_add_u64(&a->s[0], (unsigned long long)rescale(sx, s_row, s_glob));
-      red_add_u64(&a->s[1], (unsigned long long)rescale(sy, s_row, s_glob));
-      if (D == 3) red_add_u64(&a->s[2], (unsigned long long)rescale(sz, s_row, s_glob));
-      red_add_u64(&a->cnt, (unsigned long long)cnt);
-    }
-    pa = pa && !ga;
-    pb = pb && !gb;
-  }
-}
-
 // Tile epilogue shared by k_assign and k_accum_labels: residuals p - c of
 // all the tile's points (4 rows x 2 per lane) in 32-bit fixed point with
 // one tile-wide power-of-two scale (256 * max|r| * 2^s < 2^31, so int32
@@ -625,17 +632,6 @@ __device__ __forceinline__ long long tile_sse(const float2 (&best)[kRowsPerWarp]
   return rescale((long long)__reduce_add_sync(0xffffffffu, q), s2, s_sse);
 }
 
-// per-row SSE in fixed point (unit 2^-s_sse), identical on every lane
-__device__ __forceinline__ long long row_sse(float d2a, float d2b, bool va, bool vb, int s_sse) {
-  float a = va ? d2a : 0.f, b = vb ? d2b : 0.f;
-  float m = warp_max_nonneg(fmaxf(a, b));
-  int s2 = m > 0.f ? min(24 - exp_bound(m), 127) : 0;
-  float sc = pow2f(s2);
-  unsigned q = (unsigned)__float2uint_rn(a * sc) + (unsigned)__float2uint_rn(b * sc);
-  unsigned s = __reduce_add_sync(0xffffffffu, q);
-  return rescale((long long)s, s2, s_sse);
-}
-
 // The 4 rows of a 256-window starting at `base` (always inside the padded
 // arrays); a point is valid if its sorted index lies in [vlo, vhi).
 __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t base, int64_t vlo,
@@ -654,16 +650,21 @@ __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t ba
   }
 }
 
-template <int D, bool BRUTE>
-__global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2) k_assign(IterArgs A) {
+template <int D, bool BRUTE, bool MULTI>
+__global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2)
+    k_assign(const __grid_constant__ IterArgs A) {
   __shared__ float4 s_c[kAssignWarps][kTileCap];
   __shared__ unsigned short s_r[kAssignWarps][kTileCap];
   __shared__ float slb[kAssignWarps][32];
-  if (A.early_stop && A.st->done) return;
+  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = blockIdx.x * kAssignWarps + w;
-  if (t == 0 && lane == 0) atomicAdd(&A.st->passes, 1);
-  if (t >= A.tiles_max || t >= *A.n_tiles) return;   // warp-level exit, no CTA barrier below
+  if (t >= A.n_tiles) return;   // warp-level exits, no CTA barrier below
+  const int b = MULTI ? A.tcloud[t] : 0;
+  if (MULTI && A.crun[b].done) return;
+  const Cloud& cl = MULTI ? A.clouds[b] : A.cl0;
+  const int c0 = cl.c0, c1 = cl.c0 + cl.k;
+  if (t == cl.t0 && lane == 0) A.crun[b].passes += 1;   // one writer per cloud
   const int2 se = A.tiles[t];
   const int64_t base = (int64_t)(se.x / kTilePts) * kTilePts;
 
@@ -687,14 +688,14 @@ __global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2) k_as
   float4* __restrict__ sc = s_c[w];
   unsigned short* __restrict__ sr = s_r[w];
   if (BRUTE) {
-    for (int c0 = 0; c0 < A.k; c0 += kTileCap) {
-      const int m = min(kTileCap, A.k - c0);
+    for (int j0 = c0; j0 < c1; j0 += kTileCap) {
+      const int m = min(kTileCap, c1 - j0);
       __syncwarp();
-      for (int i = lane; i < m; i += 32) sc[i] = A.cw[c0 + i];
+      for (int i = lane; i < m; i += 32) sc[i] = A.cw[j0 + i];
       __syncwarp();
       eval_list<D>(sc, nullptr, m, P, best, bid);
     }
-    evals = (unsigned long long)A.k * nv_tile;
+    evals = (unsigned long long)cl.k * nv_tile;
   } else {
     const int q = A.tcnt[t];
     if (q <= 32) {
@@ -757,29 +758,29 @@ __global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2) k_as
       const float4 tlo = A.tbox[2 * t], thi = A.tbox[2 * t + 1];
       float u = INFINITY;
 #pragma unroll 8
-      for (int j = lane; j < A.k; j += 32) {
+      for (int j = c0 + lane; j < c1; j += 32) {
         const float4 c = __ldg(&A.cw[j]);
         u = fminf(u, maxd2(tlo, thi, c.x, c.y, c.z, D));
       }
       const float u2k = warp_min_nonneg(u) * kKeep;
       const unsigned lt = (1u << lane) - 1u;
       int cnt = 0;
-      for (int j0 = 0; j0 < A.k; j0 += 4 * 32) {
+      for (int j0 = c0; j0 < c1; j0 += 4 * 32) {
         float4 c[4];
 #pragma unroll
         for (int b4 = 0; b4 < 4; ++b4) {
           const int j = j0 + b4 * 32 + lane;
-          c[b4] = j < A.k ? __ldg(&A.cw[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          c[b4] = j < c1 ? __ldg(&A.cw[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int b4 = 0; b4 < 4; ++b4) {
           const int j = j0 + b4 * 32 + lane;
-          const bool keep = j < A.k && mind2(tlo, thi, c[b4].x, c[b4].y, c[b4].z, D) <= u2k;
+          const bool keep = j < c1 && mind2(tlo, thi, c[b4].x, c[b4].y, c[b4].z, D) <= u2k;
           const unsigned bal = __ballot_sync(0xffffffffu, keep);
           if (keep) sc[cnt + __popc(bal & lt)] = c[b4];
           cnt += __popc(bal);
         }
-        if (cnt > kTileCap - 4 * 32 || j0 + 4 * 32 >= A.k) {
+        if (cnt > kTileCap - 4 * 32 || j0 + 4 * 32 >= c1) {
           __syncwarp();
           eval_list<D>(sc, nullptr, cnt, P, best, bid);
           evals += (unsigned long long)cnt * nv_tile;
@@ -790,8 +791,7 @@ __global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2) k_as
     }
   }
 
-  int s_glob, s_sse;
-  fixed_exponents(A.st, A.n, &s_glob, &s_sse);
+  const int s_glob = A.crun[b].s_glob, s_sse = A.crun[b].s_sse;
   long long sse = 0;
   int changed = 0;
 #pragma unroll
@@ -815,17 +815,17 @@ __global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2) k_as
   accumulate_tile<D>(A, P.x, P.y, P.z, bid, va, vb, s_glob);
   changed = __reduce_add_sync(0xffffffffu, changed);
   if (lane == 0) {
-    Slot& s = A.slots[t & (kSlots - 1)];
-    red_add_u64(&s.sse, (unsigned long long)sse);
-    if (changed) red_add_u64(&s.changed, (unsigned long long)changed);
-    red_add_u64(&s.evals, evals);
+    CloudAcc& ca = A.cacc[b];
+    red_add_u64(&ca.sse[t & (kCloudSlots - 1)], (unsigned long long)sse);
+    if (changed) red_add_u64(&ca.changed[t & (kCloudSlots - 1)], (unsigned long long)changed);
+    red_add_u64(&A.slots[t & (kSlots - 1)].evals, evals);
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_accum_labels: residual sums for a caller-given labelling (dkm_update).
-// One warp per tile, grouped exactly like k_assign, so both produce the same
-// sums bit for bit for the same labels.
+// k_accum_labels: residual sums for a caller-given labelling (dkm_update;
+// cloud-local labels).  One warp per tile, grouped exactly like k_assign,
+// so both produce the same sums bit for bit for the same labels.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
@@ -833,14 +833,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
                                                                const uint32_t* __restrict__ perm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = blockIdx.x * kWarpsPerBlock + w;
-  if (t >= A.tiles_max || t >= *A.n_tiles) return;
+  if (t >= A.n_tiles) return;
   const int2 se = A.tiles[t];
+  const int b = A.tcloud[t];
+  const int c0 = A.clouds[b].c0, kb = A.clouds[b].k;
   const int64_t base = (int64_t)(se.x / kTilePts) * kTilePts;
   float2 x[kRowsPerWarp], y[kRowsPerWarp], z[kRowsPerWarp];
   bool va[kRowsPerWarp], vb[kRowsPerWarp];
   load_points(A, D, base, se.x, se.y, x, y, z, va, vb);
-  int s_glob, s_sse;
-  fixed_exponents(A.st, A.n, &s_glob, &s_sse);
   int bad = 0;
   int2 lab[kRowsPerWarp];
   bool oka[kRowsPerWarp], okb[kRowsPerWarp];
@@ -849,19 +849,19 @@ __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
     const int64_t i = base + r * kRowPts + 2 * lane;
     const int la = va[r] ? ulab[perm[i]] : 0;
     const int lb = vb[r] ? ulab[perm[i + 1]] : 0;
-    oka[r] = va[r] && la >= 0 && la < A.k;
-    okb[r] = vb[r] && lb >= 0 && lb < A.k;
+    oka[r] = va[r] && la >= 0 && la < kb;
+    okb[r] = vb[r] && lb >= 0 && lb < kb;
     bad |= (va[r] && !oka[r]) || (vb[r] && !okb[r]);
-    lab[r] = make_int2(oka[r] ? la : 0, okb[r] ? lb : 0);
+    lab[r] = make_int2(c0 + (oka[r] ? la : 0), c0 + (okb[r] ? lb : 0));
   }
-  accumulate_tile<D>(A, x, y, z, lab, oka, okb, s_glob);
+  accumulate_tile<D>(A, x, y, z, lab, oka, okb, A.crun[b].s_glob);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&A.st->label_err, 1);
 }
 
 // ---------------------------------------------------------------------------
-// k_finalize: labels back to the caller's order; optional SSE against the
-// current centroids (same FP32 distance expression, fixed-point sum).
-// One warp per 256-window of the sorted order.
+// k_finalize: labels back to the caller's order as cloud-local indices;
+// optional SSE against the current centroids (same FP32 distance
+// expression, fixed-point tile sums per cloud).  One warp per tile.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kBlockThreads) k_finalize(IterArgs A,
@@ -869,40 +869,41 @@ __global__ void __launch_bounds__(kBlockThreads) k_finalize(IterArgs A,
                                                            int32_t* __restrict__ labels_out,
                                                            int do_sse) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t win = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-  const int64_t base = win * kTilePts;
-  if (base >= A.n) return;
-  int s_glob, s_sse;
-  fixed_exponents(A.st, A.n, &s_glob, &s_sse);
-  long long sse = 0;
+  const int t = blockIdx.x * kWarpsPerBlock + w;
+  if (t >= A.n_tiles) return;
+  const int2 se = A.tiles[t];
+  const int b = A.tcloud[t];
+  const int c0 = A.clouds[b].c0;
+  const int64_t base = (int64_t)(se.x / kTilePts) * kTilePts;
+  float2 x[kRowsPerWarp], y[kRowsPerWarp], z[kRowsPerWarp];
+  bool va[kRowsPerWarp], vb[kRowsPerWarp];
+  load_points(A, D, base, se.x, se.y, x, y, z, va, vb);
+  float2 d2[kRowsPerWarp];
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
     const int64_t i = base + r * kRowPts + 2 * lane;
-    if (base + r * kRowPts >= A.n) break;
-    const bool va = i < A.n, vb = i + 1 < A.n;
-    const int la = va ? A.lab[i] : 0, lb = vb ? A.lab[i + 1] : 0;
+    const int la = va[r] ? A.lab[i] : c0, lb = vb[r] ? A.lab[i + 1] : c0;
     if (labels_out) {
-      if (va) labels_out[perm[i]] = la;
-      if (vb) labels_out[perm[i + 1]] = lb;
+      if (va[r]) labels_out[perm[i]] = la - c0;
+      if (vb[r]) labels_out[perm[i + 1]] = lb - c0;
     }
+    d2[r] = make_float2(0.f, 0.f);
     if (do_sse) {
-      float d2a = 0.f, d2b = 0.f;
-      if (va) {
-        float4 c = __ldg(&A.cw[la]);
-        float dx = __fadd_rn(A.xs[i], -c.x), dy = __fadd_rn(A.ys[i], -c.y);
-        d2a = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-        if (D == 3) { float dz = __fadd_rn(A.zs[i], -c.z); d2a = __fmaf_rn(dz, dz, d2a); }
-      }
-      if (vb) {
-        float4 c = __ldg(&A.cw[lb]);
-        float dx = __fadd_rn(A.xs[i + 1], -c.x), dy = __fadd_rn(A.ys[i + 1], -c.y);
-        d2b = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-        if (D == 3) { float dz = __fadd_rn(A.zs[i + 1], -c.z); d2b = __fmaf_rn(dz, dz, d2b); }
-      }
-      sse += row_sse(d2a, d2b, va, vb, s_sse);
+      const float4 ca = __ldg(&A.cw[la]), cb = __ldg(&A.cw[lb]);
+      float dx = __fadd_rn(x[r].x, -ca.x), dy = __fadd_rn(y[r].x, -ca.y);
+      float s = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+      if (D == 3) { float dz = __fadd_rn(z[r].x, -ca.z); s = __fmaf_rn(dz, dz, s); }
+      d2[r].x = s;
+      dx = __fadd_rn(x[r].y, -cb.x); dy = __fadd_rn(y[r].y, -cb.y);
+      s = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+      if (D == 3) { float dz = __fadd_rn(z[r].y, -cb.z); s = __fmaf_rn(dz, dz, s); }
+      d2[r].y = s;
     }
   }
-  if (do_sse && lane == 0) red_add_u64(&A.slots[win & (kSlots - 1)].sse, (unsigned long long)sse);
+  if (do_sse) {
+    const long long sse = tile_sse(d2, va, vb, A.crun[b].s_sse);
+    if (lane == 0) red_add_u64(&A.cacc[b].sse[t & (kCloudSlots - 1)], (unsigned long long)sse);
+  }
 }
 
 __global__ void k_export(const float4* __restrict__ cw, int k, int d, float* __restrict__ out) {
@@ -919,8 +920,8 @@ __global__ void k_export(const float4* __restrict__ cw, int k, int d, float* __r
 // ---------------------------------------------------------------------------
 static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-cudaError_t launch_reset_run(DevState* st, cudaStream_t s) {
-  k_reset_run<<<1, 1, 0, s>>>(st);
+cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s) {
+  k_reset_run<<<ceil_div(A.B, 256), 256, 0, s>>>(A.st, A.crun, A.cacc, A.B);
   return cudaGetLastError();
 }
 
@@ -932,19 +933,27 @@ cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const fl
 }
 
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
-  k_search<<<ceil_div(A.tiles_max, kSearchWarps), 32 * kSearchWarps, 0, s>>>(A, par, d);
+  const int g = ceil_div(A.n_tiles, kSearchWarps);
+  if (A.B > 1) k_search<true><<<g, 32 * kSearchWarps, 0, s>>>(A, par, d);
+  else k_search<false><<<g, 32 * kSearchWarps, 0, s>>>(A, par, d);
   return cudaGetLastError();
 }
 
-cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s) {
-  const int g = ceil_div(A.tiles_max, kAssignWarps);
+template <int D, bool BRUTE>
+void assign_multi(const IterArgs& A, int g, cudaStream_t s) {
   constexpr int thr = 32 * kAssignWarps;
+  if (A.B > 1) k_assign<D, BRUTE, true><<<g, thr, 0, s>>>(A);
+  else k_assign<D, BRUTE, false><<<g, thr, 0, s>>>(A);
+}
+
+cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s) {
+  const int g = ceil_div(A.n_tiles, kAssignWarps);
   if (d == 3) {
-    if (brute) k_assign<3, true><<<g, thr, 0, s>>>(A);
-    else k_assign<3, false><<<g, thr, 0, s>>>(A);
+    if (brute) assign_multi<3, true>(A, g, s);
+    else assign_multi<3, false>(A, g, s);
   } else {
-    if (brute) k_assign<2, true><<<g, thr, 0, s>>>(A);
-    else k_assign<2, false><<<g, thr, 0, s>>>(A);
+    if (brute) assign_multi<2, true>(A, g, s);
+    else assign_multi<2, false>(A, g, s);
   }
   return cudaGetLastError();
 }
@@ -956,7 +965,7 @@ cudaError_t launch_collect(const IterArgs& A, int t, cudaStream_t s) {
 
 cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
                                 const uint32_t* perm, cudaStream_t s) {
-  const int g = ceil_div(A.tiles_max, kWarpsPerBlock);
+  const int g = ceil_div(A.n_tiles, kWarpsPerBlock);
   if (d == 3) k_accum_labels<3><<<g, kBlockThreads, 0, s>>>(A, ulab, perm);
   else k_accum_labels<2><<<g, kBlockThreads, 0, s>>>(A, ulab, perm);
   return cudaGetLastError();
@@ -964,7 +973,7 @@ cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
 
 cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int32_t* labels_out,
                             int do_sse, cudaStream_t s) {
-  const int g = ceil_div(A.n_windows, kWarpsPerBlock);
+  const int g = ceil_div(A.n_tiles, kWarpsPerBlock);
   if (d == 3) k_finalize<3><<<g, kBlockThreads, 0, s>>>(A, perm, labels_out, do_sse);
   else k_finalize<2><<<g, kBlockThreads, 0, s>>>(A, perm, labels_out, do_sse);
   return cudaGetLastError();

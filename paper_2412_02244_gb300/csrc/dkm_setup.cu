@@ -10,11 +10,15 @@
 // axis-aligned bounding box per tile.  Points never move, so the boxes stay
 // valid for the whole run.
 //
-//   k_bbox         bounding box of the input (+ non-finite / range check)
-//   k_morton       30-bit Morton key per point (3 x 10 or 2 x 15 bits)
+//   k_bbox         per-cloud bounding boxes (+ non-finite / range check)
+//   k_morton       32-bit key per point: cloud index above a Morton code of
+//                  mb bits per axis on the cloud's own box (mb = 10 in 3D
+//                  and 15 in 2D for a single cloud, fewer when the cloud
+//                  index needs the top bits)
 //   k_rs_*         stable LSD radix sort of (key, index), 8-bit digits
 //   k_gather       sorted structure-of-arrays copy of the points
-//   k_levels       how many Morton cubes each level would cut the order into
+//   k_levels       per cloud, how many Morton cubes each level would cut
+//                  the order into
 //   k_tiles_*      tiles: 256-point windows split at cube boundaries
 //   k_tile_boxes   per-tile AABBs
 #include "dkm_host.h"
@@ -27,15 +31,33 @@ constexpr int kRsTile = kRsThreads * kRsItems;   // 2048 keys per CTA
 constexpr float kMaxAbsCoord = 1.0e18f;          // larger coordinates are rejected
 
 // ---------------------------------------------------------------------------
-// bounding box of an n x d row-major array; which = 0 -> pbox, 1 -> cbox
+// Cloud of row i: the b with seg[b] <= i < seg[b + 1] (seg has B + 1
+// ascending entries, seg[0] = 0).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int64_t n, int d,
+__device__ __forceinline__ int seg_of(const int64_t* __restrict__ seg, int B, int64_t i) {
+  int lo = 0, hi = B;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (seg[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Per-cloud bounding boxes of an n x d row-major array cut into B segments
+// (seg, B + 1 entries): blockIdx.y = cloud, blockIdx.x strides over its
+// rows.  which = 0 -> CloudRun.pbox, 1 -> CloudRun.cbox.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int d,
+                                              const int64_t* __restrict__ seg, CloudRun* crun,
                                               DevState* st, int which) {
+  const int b = blockIdx.y;
+  const int64_t r0 = seg[b], r1 = seg[b + 1];
   float lo[3] = {INFINITY, INFINITY, INFINITY};
   float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   int bad = 0;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += stride) {
     for (int a = 0; a < d; ++a) {
       float v = p[i * d + a];
       if (!(fabsf(v) <= kMaxAbsCoord)) {   // also catches NaN
@@ -54,7 +76,7 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int64
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
-    unsigned* box = which == 0 ? st->pbox : st->cbox;
+    unsigned* box = which == 0 ? crun[b].pbox : crun[b].cbox;
     for (int a = 0; a < d; ++a) {
       if (lo[a] <= hi[a]) {
         atomicMin(&box[a], ord_of(lo[a]));
@@ -65,24 +87,30 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int64
   }
 }
 
-// reset a box to the empty box (2D contexts pin the z range to [0, 0]) and
-// clear the bad-input flag
-__global__ void k_reset_boxes(DevState* st, int d, int which_mask) {
-  int t = threadIdx.x;
-  if (t < 3) {
-    for (int w = 0; w < 2; ++w) {
-      if (!(which_mask & (1 << w))) continue;
-      unsigned* box = w == 0 ? st->pbox : st->cbox;
-      if (t < d) {
-        box[t] = 0xffffffffu;
-        box[3 + t] = 0u;
-      } else {
-        box[t] = ord_of(0.f);
-        box[3 + t] = ord_of(0.f);
-      }
+// reset the selected boxes of every cloud to the empty box (2D contexts pin
+// the z range to [0, 0]) and clear the bad-input flag
+__global__ void k_reset_boxes(CloudRun* crun, int B, DevState* st, int d, int which_mask) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) st->bad = 0;
+  if (b >= B) return;
+  for (int w = 0; w < 2; ++w) {
+    if (!(which_mask & (1 << w))) continue;
+    unsigned* box = w == 0 ? crun[b].pbox : crun[b].cbox;
+    for (int t = 0; t < 3; ++t) {
+      box[t] = t < d ? 0xffffffffu : ord_of(0.f);
+      box[3 + t] = t < d ? 0u : ord_of(0.f);
     }
   }
-  if (t == 0) st->bad = 0;
+}
+
+// fixed-point exponents of every cloud for the current run
+__global__ void k_exponents(const Cloud* __restrict__ clouds, CloudRun* crun, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int sg, ss;
+  fixed_exponents_box(crun[b].pbox, crun[b].cbox, clouds[b].n, &sg, &ss);
+  crun[b].s_glob = sg;
+  crun[b].s_sse = ss;
 }
 
 // ---------------------------------------------------------------------------
@@ -106,21 +134,29 @@ __device__ __forceinline__ uint32_t spread2(uint32_t v) {   // 15 bits -> every 
   return v;
 }
 
+// Key of a point of cloud b: b in the bits above d * mb, then the Morton
+// code of its mb-bit-per-axis lattice coordinates on the cloud's own box.
 __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ p, int64_t n, int d,
-                                                float3 lo, float inv, uint32_t* __restrict__ keys,
+                                                const int64_t* __restrict__ seg, int B,
+                                                const Cloud* __restrict__ clouds, int mb,
+                                                uint32_t* __restrict__ keys,
                                                 uint32_t* __restrict__ vals) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float qmax = d == 3 ? 1023.f : 32767.f;
-  float q0 = fminf(fmaxf((p[i * d + 0] - lo.x) * inv, 0.f), qmax);
-  float q1 = fminf(fmaxf((p[i * d + 1] - lo.y) * inv, 0.f), qmax);
+  const int b = B > 1 ? seg_of(seg, B, i) : 0;
+  const Cloud& c = clouds[b];
+  const float qmax = (float)((1u << mb) - 1u);
+  const float inv = c.minv;
+  float q0 = fminf(fmaxf((p[i * d + 0] - c.mlo[0]) * inv, 0.f), qmax);
+  float q1 = fminf(fmaxf((p[i * d + 1] - c.mlo[1]) * inv, 0.f), qmax);
   uint32_t key;
   if (d == 3) {
-    float q2 = fminf(fmaxf((p[i * d + 2] - lo.z) * inv, 0.f), qmax);
+    float q2 = fminf(fmaxf((p[i * d + 2] - c.mlo[2]) * inv, 0.f), qmax);
     key = spread3((uint32_t)q0) | (spread3((uint32_t)q1) << 1) | (spread3((uint32_t)q2) << 2);
   } else {
     key = spread2((uint32_t)q0) | (spread2((uint32_t)q1) << 1);
   }
+  if (B > 1) key |= (uint32_t)b << (d * mb);
   keys[i] = key;
   vals[i] = (uint32_t)i;
 }
@@ -272,43 +308,66 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ p, int
 }
 
 // ---------------------------------------------------------------------------
-// Tiling.  Level l of the Morton code splits the domain into 2^(d*l) cubes;
-// a cube's points are contiguous in the sorted order.  k_levels counts, for
-// each level, how many sorted neighbours first differ at that level (a cube
-// boundary of that level and every finer one).  The host then picks the
-// finest level whose cube count keeps the extra tiles below 1/8.
+// Tiling.  Level l of a cloud's Morton code splits its box into 2^(d*l)
+// cubes; a cube's points are contiguous in the sorted order.  k_levels
+// counts, per cloud and level, how many sorted neighbours first differ at
+// that level (a cube boundary of that level and every finer one); level 0
+// is a cloud boundary.  The host then picks, per cloud, the finest level
+// whose cube count keeps the cloud's extra tiles within a set fraction.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int first_diff_level(uint32_t a, uint32_t b, int d) {
+__device__ __forceinline__ int first_diff_level(uint32_t a, uint32_t b, int d, int mb) {
   const uint32_t x = a ^ b;
   if (x == 0) return kMaxLevels;          // same cube at every level
   const int p = 31 - __clz(x);            // highest differing bit
-  const int L = d == 3 ? 10 : 15;
-  return L - p / d;                        // 1 = the coarsest level
+  if (p >= d * mb) return 0;              // different clouds
+  return mb - p / d;                       // 1 = the coarsest level
 }
 
+__device__ __forceinline__ int cloud_of_key(uint32_t key, int d, int mb, int B) {
+  return B > 1 ? (int)(key >> (d * mb)) : 0;
+}
+
+// hist: B x (kMaxLevels + 1) counters.  With smem_hist the CTA first
+// counts in shared memory (B * (kMaxLevels + 1) words, dynamic).
 __global__ void __launch_bounds__(256) k_levels(const uint32_t* __restrict__ keys, int64_t n,
-                                                int d, unsigned long long* __restrict__ hist) {
-  __shared__ unsigned int h[kMaxLevels + 1];
-  if (threadIdx.x <= kMaxLevels) h[threadIdx.x] = 0;
-  __syncthreads();
+                                                int d, int mb, int B, int smem_hist,
+                                                unsigned long long* __restrict__ hist) {
+  extern __shared__ unsigned int h[];
+  const int nh = B * (kMaxLevels + 1);
+  if (smem_hist) {
+    for (int q = threadIdx.x; q < nh; q += blockDim.x) h[q] = 0;
+    __syncthreads();
+  }
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += stride)
-    atomicAdd(&h[first_diff_level(keys[i - 1], keys[i], d)], 1u);
-  __syncthreads();
-  if (threadIdx.x <= kMaxLevels && h[threadIdx.x])
-    atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += stride) {
+    const uint32_t kb = keys[i];
+    const int q = cloud_of_key(kb, d, mb, B) * (kMaxLevels + 1) + first_diff_level(keys[i - 1], kb, d, mb);
+    if (smem_hist) atomicAdd(&h[q], 1u);
+    else atomicAdd(&hist[q], 1ull);
+  }
+  if (smem_hist) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < nh; q += blockDim.x)
+      if (h[q]) atomicAdd(&hist[q], (unsigned long long)h[q]);
+  }
 }
 
-// a sorted position starts a tile if it starts a 256-window or a cube
+// a sorted position starts a tile if it starts a 256-window or its key
+// differs from its predecessor's above the cloud's cut shift (a cloud
+// boundary always differs there)
 __device__ __forceinline__ bool tile_starts(const uint32_t* __restrict__ keys, int64_t i,
-                                            int shift) {
+                                            const Cloud* __restrict__ clouds, int d, int mb,
+                                            int B) {
   if ((i & (kTilePts - 1)) == 0) return true;
-  return (keys[i] >> shift) != (keys[i - 1] >> shift);
+  const uint32_t k1 = keys[i];
+  const int shift = clouds[cloud_of_key(k1, d, mb, B)].shift;
+  return (k1 >> shift) != (keys[i - 1] >> shift);
 }
 
 // one warp per 256-window: number of tiles that start in it
 __global__ void __launch_bounds__(256) k_tiles_count(const uint32_t* __restrict__ keys, int64_t n,
-                                                     int shift, int n_windows,
+                                                     const Cloud* __restrict__ clouds, int d,
+                                                     int mb, int B, int n_windows,
                                                      int* __restrict__ wcnt) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -316,7 +375,7 @@ __global__ void __launch_bounds__(256) k_tiles_count(const uint32_t* __restrict_
   int c = 0;
   for (int j = 0; j < kTilePts / 32; ++j) {
     const int64_t i = w * kTilePts + j * 32 + lane;
-    c += __popc(__ballot_sync(0xffffffffu, i < n && tile_starts(keys, i, shift)));
+    c += __popc(__ballot_sync(0xffffffffu, i < n && tile_starts(keys, i, clouds, d, mb, B)));
   }
   if (lane == 0) wcnt[w] = c;
 }
@@ -348,7 +407,8 @@ __global__ void __launch_bounds__(1024) k_scan_windows(const int* __restrict__ w
 
 // one warp per window: write [start, end) of every tile that starts in it
 __global__ void __launch_bounds__(256) k_tiles_write(const uint32_t* __restrict__ keys, int64_t n,
-                                                     int shift, int n_windows,
+                                                     const Cloud* __restrict__ clouds, int d,
+                                                     int mb, int B, int n_windows,
                                                      const int* __restrict__ wbase,
                                                      int2* __restrict__ tiles) {
   __shared__ int s_pos[8][kTilePts + 1];
@@ -359,7 +419,7 @@ __global__ void __launch_bounds__(256) k_tiles_write(const uint32_t* __restrict_
   int c = 0;
   for (int j = 0; j < kTilePts / 32; ++j) {
     const int64_t i = w * kTilePts + j * 32 + lane;
-    const bool f = i < n && tile_starts(keys, i, shift);
+    const bool f = i < n && tile_starts(keys, i, clouds, d, mb, B);
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (f) s_pos[wl][c + __popc(bal & lt)] = (int)i;
     c += __popc(bal);
@@ -371,16 +431,19 @@ __global__ void __launch_bounds__(256) k_tiles_write(const uint32_t* __restrict_
   for (int j = lane; j < c; j += 32) tiles[base + j] = make_int2(s_pos[wl][j], s_pos[wl][j + 1]);
 }
 
-// one warp per tile: AABB of its points
+// one warp per tile: AABB of its points, its cloud, and each cloud's first
+// tile (a tile never spans two clouds)
 __global__ void __launch_bounds__(256) k_tile_boxes(const float* __restrict__ xs,
                                                     const float* __restrict__ ys,
                                                     const float* __restrict__ zs, int d,
-                                                    const int2* __restrict__ tiles,
-                                                    const int* __restrict__ n_tiles,
-                                                    int tiles_max, float4* __restrict__ tbox) {
+                                                    const int2* __restrict__ tiles, int n_tiles,
+                                                    const uint32_t* __restrict__ keys, int mb,
+                                                    int B, float4* __restrict__ tbox,
+                                                    int* __restrict__ tcloud,
+                                                    Cloud* __restrict__ clouds) {
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (t >= tiles_max || t >= *n_tiles) return;
+  if (t >= n_tiles) return;
   const int2 se = tiles[t];
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int i = se.x + lane; i < se.y; i += 32) {
@@ -398,6 +461,9 @@ __global__ void __launch_bounds__(256) k_tile_boxes(const float* __restrict__ xs
   if (lane == 0) {
     tbox[2 * t] = make_float4(lo[0], lo[1], lo[2], 0.f);
     tbox[2 * t + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    const int b = cloud_of_key(keys[se.x], d, mb, B);
+    tcloud[t] = b;
+    if (se.x == 0 || cloud_of_key(keys[se.x - 1], d, mb, B) != b) clouds[b].t0 = t;
   }
 }
 
@@ -410,17 +476,23 @@ static int grid_for(int64_t n, int threads, int cap) {
   return (int)(g > cap ? cap : g);
 }
 
-cudaError_t launch_bbox(const float* p, int64_t n, int d, DevState* st, int which, int d_ctx,
-                        cudaStream_t s) {
-  k_reset_boxes<<<1, 32, 0, s>>>(st, d_ctx, which == 0 ? 1 : 2);
-  k_bbox<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(p, n, d, st, which);
+cudaError_t launch_bbox(const float* p, int d, const int64_t* seg, int B, int64_t max_rows,
+                        CloudRun* crun, DevState* st, int which, int d_ctx, cudaStream_t s) {
+  k_reset_boxes<<<(B + 255) / 256, 256, 0, s>>>(crun, B, st, d_ctx, which == 0 ? 1 : 2);
+  dim3 g(grid_for(max_rows, 256 * 4, 152 * 8), B);
+  k_bbox<<<g, 256, 0, s>>>(p, d, seg, crun, st, which);
   return cudaGetLastError();
 }
 
-cudaError_t launch_morton(const float* p, int64_t n, int d, const float* lo, float inv,
-                          uint32_t* keys, uint32_t* vals, cudaStream_t s) {
-  float3 l = make_float3(lo[0], lo[1], d == 3 ? lo[2] : 0.f);
-  k_morton<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, n, d, l, inv, keys, vals);
+cudaError_t launch_exponents(const Cloud* clouds, CloudRun* crun, int B, cudaStream_t s) {
+  k_exponents<<<(B + 255) / 256, 256, 0, s>>>(clouds, crun, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_morton(const float* p, int64_t n, int d, const int64_t* seg, int B,
+                          const Cloud* clouds, int mb, uint32_t* keys, uint32_t* vals,
+                          cudaStream_t s) {
+  k_morton<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, n, d, seg, B, clouds, mb, keys, vals);
   return cudaGetLastError();
 }
 
@@ -448,27 +520,37 @@ cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* orde
   return cudaGetLastError();
 }
 
-cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, unsigned long long* hist,
-                          cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (kMaxLevels + 1), s);
+constexpr int kLevelSmemMax = 48 * 1024;
+
+cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,
+                          unsigned long long* hist, cudaStream_t s) {
+  const size_t nh = (size_t)B * (kMaxLevels + 1);
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nh, s);
   if (e != cudaSuccess) return e;
-  k_levels<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(keys, n, d, hist);
+  const size_t smem = nh * sizeof(unsigned int);
+  const int use_smem = smem <= (size_t)kLevelSmemMax;
+  // shared histograms pay a flush per CTA: fewer CTAs when they are large
+  const int cap = use_smem ? (nh > 1024 ? 152 * 2 : 152 * 8) : 152 * 8;
+  k_levels<<<grid_for(n, 256, cap), 256, use_smem ? smem : 0, s>>>(keys, n, d, mb, B, use_smem,
+                                                                   hist);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tiles(const uint32_t* keys, int64_t n, int shift, int n_windows, int* wcnt,
-                         int* wbase, int* n_tiles, int2* tiles, cudaStream_t s) {
+cudaError_t launch_tiles(const uint32_t* keys, int64_t n, const Cloud* clouds, int d, int mb,
+                         int B, int n_windows, int* wcnt, int* wbase, int* n_tiles, int2* tiles,
+                         cudaStream_t s) {
   const int g = (n_windows + 7) / 8;
-  k_tiles_count<<<g, 256, 0, s>>>(keys, n, shift, n_windows, wcnt);
+  k_tiles_count<<<g, 256, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, wcnt);
   k_scan_windows<<<1, 1024, 0, s>>>(wcnt, n_windows, wbase, n_tiles);
-  k_tiles_write<<<g, 256, 0, s>>>(keys, n, shift, n_windows, wbase, tiles);
+  k_tiles_write<<<g, 256, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, wbase, tiles);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
-                              const int2* tiles, const int* n_tiles, int tiles_max, float4* tbox,
-                              cudaStream_t s) {
-  k_tile_boxes<<<(tiles_max + 7) / 8, 256, 0, s>>>(xs, ys, zs, d, tiles, n_tiles, tiles_max, tbox);
+                              const int2* tiles, int n_tiles, const uint32_t* keys, int mb, int B,
+                              float4* tbox, int* tcloud, Cloud* clouds, cudaStream_t s) {
+  k_tile_boxes<<<(n_tiles + 7) / 8, 256, 0, s>>>(xs, ys, zs, d, tiles, n_tiles, keys, mb, B, tbox,
+                                                 tcloud, clouds);
   return cudaGetLastError();
 }
 

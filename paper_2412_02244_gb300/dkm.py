@@ -57,6 +57,13 @@ class dkm_stats(ctypes.Structure):
                 ("tiles", ctypes.c_int64), ("tile_level", ctypes.c_int), ("passes", ctypes.c_int)]
 
 
+class dkm_tuning(ctypes.Structure):
+    _fields_ = [("cells_per_centroid", ctypes.c_float), ("tile_cut_div", ctypes.c_int),
+                ("row_filter_min", ctypes.c_int), ("ms_per_pass", ctypes.c_float),
+                ("ms_per_pass_before", ctypes.c_float), ("trials", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 # (name, restype, argtypes); "status" functions return dkm_status
@@ -83,6 +90,21 @@ _SIGS = [
                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(dkm_options)]),
+    ("dkm_create_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.POINTER(dkm_options)]),
+    ("dkm_run_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    ("dkm_fit_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(dkm_options)]),
+    ("dkm_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dkm_tuning)]),
+    ("dkm_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dkm_tuning)]),
+    ("dkm_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(dkm_tuning)]),
     ("dkm_query_memory", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
                                         ctypes.POINTER(ctypes.c_size_t)]),
     ("dkm_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dkm_plan_info)]),
@@ -187,9 +209,9 @@ def dkm_plan(n: int, d: int, k: int, bbox_lo, bbox_hi,
 class Context:
     """Owns one dkm_ctx handle (dkm_destroy on close / garbage collection)."""
 
-    def __init__(self, handle: int, n: int, d: int, k: int):
+    def __init__(self, handle: int, n: int, d: int, k: int, B: int = 1):
         self.handle = ctypes.c_void_p(handle)
-        self.n, self.d, self.k = n, d, k
+        self.n, self.d, self.k, self.B = n, d, k, B
 
     def close(self) -> None:
         if self.handle and self.handle.value:
@@ -263,6 +285,83 @@ def dkm_fit(points, n: int, d: int, k: int, init_centroids, max_iter: int, centr
                          ctypes.byref(sse), ctypes.byref(opts) if opts is not None else None),
            "dkm_fit")
     return it.value, sse.value
+
+
+def _batch_sizes(offsets, ks):
+    off = np.ascontiguousarray(np.asarray(offsets), dtype=np.int64)
+    kv = np.ascontiguousarray(np.asarray(ks), dtype=np.int32)
+    if off.ndim != 1 or kv.ndim != 1 or off.size != kv.size + 1:
+        raise ValueError("offsets must have len(ks) + 1 entries")
+    return off, kv
+
+
+def dkm_create_batched(points, offsets, d: int, ks,
+                       opts: Optional[dkm_options] = None) -> Context:
+    """Context over B clouds: points[offsets[b]:offsets[b+1]] with ks[b] clusters."""
+    off, kv = _batch_sizes(offsets, ks)
+    n, B, K = int(off[-1]), int(kv.size), int(kv.sum())
+    p, _keep = _arr(points, "float32", n * d, "points")
+    h = ctypes.c_void_p()
+    _check(lib().dkm_create_batched(ctypes.byref(h), p, off.ctypes.data, B, d, kv.ctypes.data,
+                                    ctypes.byref(opts) if opts is not None else None),
+           "dkm_create_batched")
+    return Context(h.value, n, d, K, B)
+
+
+def dkm_run_batched(ctx: Context, init_centroids, max_iter: int, centroids_out=None,
+                    labels_out=None) -> Tuple[np.ndarray, np.ndarray]:
+    """Lloyd on every cloud; returns (passes per cloud, final SSE per cloud)."""
+    i, _k1 = _arr(init_centroids, "float32", ctx.k * ctx.d, "init_centroids")
+    c, _k2 = _arr(centroids_out, "float32", ctx.k * ctx.d, "centroids_out")
+    lab, _k3 = _arr(labels_out, "int32", ctx.n, "labels_out")
+    it = np.zeros(ctx.B, np.int32)
+    sse = np.zeros(ctx.B, np.float64)
+    _check(lib().dkm_run_batched(ctx.handle, i, int(max_iter), c, lab, it.ctypes.data,
+                                 sse.ctypes.data), "dkm_run_batched")
+    return it, sse
+
+
+def dkm_fit_batched(points, offsets, d: int, ks, init_centroids, max_iter: int,
+                    centroids_out=None, labels_out=None,
+                    opts: Optional[dkm_options] = None) -> Tuple[np.ndarray, np.ndarray]:
+    off, kv = _batch_sizes(offsets, ks)
+    n, B, K = int(off[-1]), int(kv.size), int(kv.sum())
+    p, _k0 = _arr(points, "float32", n * d, "points")
+    i, _k1 = _arr(init_centroids, "float32", K * d, "init_centroids")
+    c, _k2 = _arr(centroids_out, "float32", K * d, "centroids_out")
+    lab, _k3 = _arr(labels_out, "int32", n, "labels_out")
+    it = np.zeros(B, np.int32)
+    sse = np.zeros(B, np.float64)
+    _check(lib().dkm_fit_batched(p, off.ctypes.data, B, d, kv.ctypes.data, i, int(max_iter), c,
+                                 lab, it.ctypes.data, sse.ctypes.data,
+                                 ctypes.byref(opts) if opts is not None else None),
+           "dkm_fit_batched")
+    return it, sse
+
+
+def dkm_get_tuning(ctx: Context) -> dkm_tuning:
+    out = dkm_tuning()
+    _check(lib().dkm_get_tuning(ctx.handle, ctypes.byref(out)), "dkm_get_tuning")
+    return out
+
+
+def dkm_set_tuning(ctx: Context, tuning: Optional[dkm_tuning] = None, **kw) -> None:
+    t = tuning if tuning is not None else dkm_get_tuning(ctx)
+    for k, v in kw.items():
+        if not hasattr(t, k):
+            raise AttributeError(k)
+        setattr(t, k, v)
+    _check(lib().dkm_set_tuning(ctx.handle, ctypes.byref(t)), "dkm_set_tuning")
+
+
+def dkm_autotune(ctx: Context, init_centroids, passes: int = 3,
+                 use_cache: bool = True) -> dkm_tuning:
+    """Time index settings on this context and keep the fastest."""
+    i, _k1 = _arr(init_centroids, "float32", ctx.k * ctx.d, "init_centroids")
+    out = dkm_tuning()
+    _check(lib().dkm_autotune(ctx.handle, i, int(passes), 1 if use_cache else 0,
+                              ctypes.byref(out)), "dkm_autotune")
+    return out
 
 
 def dkm_query_memory(ctx: Context) -> Tuple[int, int]:

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every function
 include/dkm.h declares, validates arguments on the host, and the grid
 planner honours the memory budget (the memory-tunable index of Section V-A)."""
+import ctypes
 import math
 import os
 import re
@@ -120,3 +121,30 @@ def test_create_validates_before_touching_the_gpu(dkm):
         dkm.dkm_create(np.zeros(8, np.float32), 4, 2, 5)     # k > n
     assert e.value.status == dkm.DKM_EINVAL
     assert "must not exceed" in dkm.dkm_last_error()
+
+
+@pytest.mark.parametrize("offsets,ks,d,msg", [
+    ([0, 5, 5, 9], [1, 1, 1], 3, "empty"),          # a cloud with no points
+    ([0, 4, 9], [5, 2], 3, "exceeds"),               # k_b > n_b
+    ([0, 4, 9], [0, 2], 3, ">= 1"),                  # k_b < 1
+    ([1, 4, 9], [1, 2], 3, "offsets[0]"),            # offsets do not start at 0
+    ([0, 4, 9], [1, 2], 4, "d must be"),             # d not 2 / 3
+])
+def test_batched_create_validates_before_touching_the_gpu(dkm, offsets, ks, d, msg):
+    n = offsets[-1]
+    with pytest.raises(dkm.DkmError) as e:
+        dkm.dkm_create_batched(np.zeros(max(n, 1) * d, np.float32), offsets, d, ks)
+    assert e.value.status == dkm.DKM_EINVAL
+    assert msg in dkm.dkm_last_error()
+
+
+def test_batched_create_rejects_bad_cloud_count(dkm):
+    status = dkm.lib().dkm_create_batched(None, None, None, 0, 3, None, None)
+    assert status == dkm.DKM_EINVAL
+    h = ctypes.c_void_p()
+    pts = np.zeros(3, np.float32)
+    off = np.zeros(2, np.int64)
+    ks = np.ones(1, np.int32)
+    status = dkm.lib().dkm_create_batched(ctypes.byref(h), pts.ctypes.data, off.ctypes.data,
+                                          70_000, 3, ks.ctypes.data, None)
+    assert status == dkm.DKM_EINVAL and "B must be" in dkm.dkm_last_error()
