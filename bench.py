@@ -183,12 +183,142 @@ def run_reference(args):
 
 
 def launches_per_step(iters: int) -> int:
-    # dkm_setup: reset_boxes, bbox, morton, 4 x (upsweep, scan, downsweep), gather, boxes
-    setup = 2 + 1 + 12 + 1 + 1
-    # dkm_run: centroid reset_boxes + bbox; graph: reset_run, prep, iters x (search, assign,
-    # centroids); finalize, collect, export
-    run = 2 + 2 + 3 * iters + 3
+    # dkm_setup: reset_boxes, bbox, morton, 4 x (upsweep, scan, downsweep), gather, levels,
+    # tiles (count, scan, write), tile boxes
+    setup = 2 + 1 + 12 + 1 + 1 + 3 + 1
+    # dkm_run: centroid reset_boxes + bbox + exponents; graph: reset_run, prep,
+    # iters x (search, assign, centroids); finalize, collect, export
+    run = 3 + 2 + 3 * iters + 3
     return setup + run
+
+
+BATCHED = dict(workload="batched3d", clouds=512, n_i="round(2^U[10,17])",
+               k_i="max(8, n_i // 100)", d=3, iterations=25, seed=4)
+SOFT = dict(workload="soft3d", clouds=64, n_i=16384, k=256, d=3, T=10, seed=5)
+
+
+def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
+    """The uneven-batch workload: 512 clouds in one context, autotuned index,
+    25 fixed passes per step (dkm_setup + dkm_run_batched), plus the same
+    passes by brute force from the run's final centroids."""
+    from paper_2412_02244_gb300 import synth
+    ws = synth.batched3d(seed=BATCHED["seed"])
+    P = np.ascontiguousarray(np.concatenate([w.points for w in ws]).astype(np.float32))
+    off = np.zeros(len(ws) + 1, np.int64)
+    off[1:] = np.cumsum([w.n for w in ws])
+    ks = np.array([w.k for w in ws], np.int32)
+    init = np.ascontiguousarray(np.concatenate([w.init for w in ws]).astype(np.float32))
+    n, K, it = int(off[-1]), int(ks.sum()), BATCHED["iterations"]
+    pts = torch.from_numpy(P).to(dev)
+    ini = torch.from_numpy(init).to(dev)
+    C = torch.empty(K * 3, dtype=torch.float32, device=dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    opts = dkm.dkm_default_options(early_stop=0, profile=1, stream=stream.cuda_stream)
+    ctx = dkm.dkm_create_batched(pts, off, 3, ks, opts)
+    tune = dkm.dkm_autotune(ctx, ini, passes=3, use_cache=False)
+
+    def step():
+        dkm.dkm_setup(ctx, pts)
+        return dkm.dkm_run_batched(ctx, ini, it, C, lab)
+
+    for _ in range(2):
+        step()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    a_ms, s_ms, u_ms, setup_ms = [], [], [], []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+        T = dkm.dkm_last_timings(ctx)
+        a_ms.append(T.assign_ms)
+        s_ms.append(T.search_ms)
+        u_ms.append(T.update_ms)
+        setup_ms.append(T.setup_ms)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / steps
+    st = dkm.dkm_last_stats(ctx)
+    per_pass = float(np.mean(s_ms) + np.mean(a_ms) + np.mean(u_ms))
+    ob = dkm.dkm_default_options(early_stop=0, profile=1, algo=dkm.DKM_ALGO_BRUTE,
+                                 stream=stream.cuda_stream)
+    cb = dkm.dkm_create_batched(pts, off, 3, ks, ob)
+    Cb = torch.empty(K * 3, dtype=torch.float32, device=dev)
+    lb = torch.empty(n, dtype=torch.int32, device=dev)
+    dkm.dkm_run_batched(cb, C, 2, Cb, lb)
+    Tb = dkm.dkm_last_timings(cb)
+    dkm.dkm_run_batched(ctx, C, 2, Cb, lb)
+    Ti = dkm.dkm_last_timings(ctx)
+    per_b = Tb.search_ms + Tb.assign_ms + Tb.update_ms
+    per_i = Ti.search_ms + Ti.assign_ms + Ti.update_ms
+    cb.close()
+    ctx.close()
+    am = float(np.mean(a_ms))
+    achieved = n * ASSIGN_BYTES_PER_POINT / (am * 1e-3) / 1e9
+    return {"config": dict(BATCHED, n_total=n, k_total=K),
+            "value": n * it / t_step, "unit": METRIC, "ms_per_step": t_step * 1e3,
+            "per_pass_ms": per_pass, "search_ms": float(np.mean(s_ms)), "assign_ms": am,
+            "update_ms": float(np.mean(u_ms)), "setup_ms": float(np.mean(setup_ms)),
+            "roofline_k_assign": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                                  "unit": "GB/s", "frac": achieved / hbm},
+            "tuning": {"cells_per_centroid": tune.cells_per_centroid,
+                       "tile_cut_div": tune.tile_cut_div, "row_filter_min": tune.row_filter_min,
+                       "ms_per_pass": tune.ms_per_pass,
+                       "ms_per_pass_default": tune.ms_per_pass_before, "trials": tune.trials},
+            "pruning": {"evals_per_point": st.evals_per_point,
+                        "candidates_per_tile": st.candidates_per_tile, "tiles": st.tiles},
+            "brute_force": {"ms_per_pass": per_b, "indexed_ms_per_pass": per_i,
+                            "speedup_indexed_over_brute": per_b / per_i if per_i > 0 else None,
+                            "from": "final centroids of the timed run, 2 passes each"},
+            "launches_per_pass": 3}
+
+
+def bench_soft(dkm, torch, dev, stream, steps: int):
+    """The differentiable workload: 64 clouds x 16384 points, k = 256; soft
+    k-means with T = 10 unrolled steps forward + backward, and the hard SSE
+    with its gradient."""
+    from paper_2412_02244_gb300 import synth
+    from paper_2412_02244_gb300.autograd import temperature
+    ws = synth.soft3d(seed=SOFT["seed"], n_clouds=SOFT["clouds"])
+    P = torch.from_numpy(np.concatenate([w.points for w in ws])).to(dev)
+    init = torch.from_numpy(np.stack([w.init for w in ws])).to(dev)
+    B, k, T = SOFT["clouds"], SOFT["k"], SOFT["T"]
+    off = np.zeros(B + 1, np.int64)
+    off[1:] = np.cumsum([w.n for w in ws])
+    tau = temperature(P, torch.from_numpy(off)).numpy()
+    ck = torch.empty((T + 1, B, k, 3), dtype=torch.float32, device=dev)
+    loss = torch.empty(B, dtype=torch.float64, device=dev)
+    gp = torch.empty_like(P)
+    gi = torch.empty_like(init)
+    gc = torch.empty_like(init)
+    dl = np.ones(B)
+    s = stream.cuda_stream
+
+    def fwd_bwd():
+        dkm.dkm_soft_forward(P, off, B, 3, k, init, T, tau, ck, loss, s)
+        dkm.dkm_soft_backward(P, off, B, 3, k, ck, T, tau, dl, gp, gi, s)
+
+    def hard():
+        dkm.dkm_hard_sse(P, off, B, 3, k, init, None, loss, gp, gc, s)
+
+    out = {"config": SOFT}
+    for name, fn in (("soft_forward_backward_ms", fwd_bwd), ("hard_sse_with_grad_ms", hard)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / steps
+    n = int(off[-1])
+    # forward: T + 1 weight passes over n x k distances; backward: recompute
+    # + adjoint, about 3 passes per step
+    out["soft_point_centroid_pairs_per_s"] = n * k * (T + 1) / (out["soft_forward_backward_ms"] * 1e-3)
+    return out
 
 
 def run_ours(args):
@@ -341,6 +471,10 @@ def run_ours(args):
                                           f"against all k=10000 centroids + update) of "
                                           f"{min(args.cpu_sample, n)} of the workload's {n} "
                                           f"points ({dt:.1f} s)"}
+    if ws == 1 and not args.no_extra:
+        ctx.close()
+        line["batched"] = bench_batched(dkm, torch, dev, stream, max(2, min(args.steps, 5)), hbm)
+        line["differentiable"] = bench_soft(dkm, torch, dev, stream, max(2, min(args.steps, 5)))
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -361,6 +495,8 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-brute", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched-cloud and differentiable side measurements")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -261,6 +261,10 @@ typedef struct {
     /* tile candidate lists longer than this are filtered again per row of
      * 64 points (default 48; >= 256 turns the row filter off) */
     int row_filter_min;
+    /* candidate lists up to this length (0 .. 32) are sorted by their box
+     * lower bound and evaluated with an early exit once the bound exceeds
+     * every point's current best (the kNN pruning rule); default 0 (off) */
+    int sort_max;
     /* dkm_autotune only: mean ms per Lloyd pass of the chosen setting and
      * of the setting the context had before, configurations timed, and
      * whether the choice came from the process-wide cache (nothing timed) */
@@ -280,7 +284,8 @@ DKM_API dkm_status dkm_set_tuning(dkm_ctx* ctx, const dkm_tuning* tuning);
 /*
  * Measure and apply the fastest setting for this context: coordinate
  * descent over cells_per_centroid {0.5, 1, 2, 4}, tile_cut_div
- * {2, 4, 8, 16, 32} and row_filter_min {16, 32, 48, 96, 256}, each
+ * {2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256} and sort_max
+ * {0, 16, 32}, each
  * setting timed (CUDA events, best of two) over `passes` Lloyd passes
  * (1 .. 64, no early stop) from init_centroids.  The context's labels and
  * centroids are overwritten by those runs.  With use_cache = 1 a setting

@@ -221,7 +221,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.ovf1 = L.take<float4>(k);
   P.ovf_cnt0 = L.take<int>(B);
   P.ovf_cnt1 = L.take<int>(B);
-  P.tlist = L.take<int>(tm * kTileCap);
+  P.tlist = L.take<float4>(tm * kTileCap);
   P.tcnt = L.take<int>(tm);
   P.cstage = L.take<float>((size_t)k * d);
   P.cstage2 = L.take<float>((size_t)k * d);
@@ -276,6 +276,7 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.track_changes = track_changes;
   A.early_stop = early_stop;
   A.row_filter_min = c->row_filter_min;
+  A.sort_max = c->sort_max;
   return A;
 }
 
@@ -589,6 +590,8 @@ dkm_status apply_tiling(dkm_ctx* c) {
   DKM_CK(cudaStreamSynchronize(c->stream));
   if (nt < 1 || nt > c->tiles_cap) return fail(DKM_EINTERNAL, "tile count %d out of range", nt);
   c->n_tiles = nt;
+  // candidate lists of the old tiles must not seed the new ones
+  DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
   DKM_CK(launch_tile_boxes(c->xs, c->ys, c->zs, c->d, c->tiles, nt, c->skeys, c->mb, c->B,
                            c->tbox, c->tcloud, c->clouds, c->stream));
   // the kernel filled each cloud's first tile: refresh the host copy
@@ -766,7 +769,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->ovf[1] = (float4*)(base + P.ovf1);
   c->ovf_cnt[0] = (int*)(base + P.ovf_cnt0);
   c->ovf_cnt[1] = (int*)(base + P.ovf_cnt1);
-  c->tlist = (int*)(base + P.tlist);
+  c->tlist = (float4*)(base + P.tlist);
   c->tcnt = (int*)(base + P.tcnt);
   c->cstage = (float*)(base + P.cstage);
   c->cstage2 = (float*)(base + P.cstage2);
@@ -883,6 +886,8 @@ dkm_status tuning_check(const dkm_ctx* c, const dkm_tuning& t) {
     return fail(DKM_EINVAL, "tile_cut_div must be in [%d, 1024] (got %d)", kMinCutDiv,
                 t.tile_cut_div);
   if (t.row_filter_min < 0) return fail(DKM_EINVAL, "row_filter_min must be >= 0");
+  if (t.sort_max < 0 || t.sort_max > 32)
+    return fail(DKM_EINVAL, "sort_max must be in [0, 32] (got %d)", t.sort_max);
   return DKM_OK;
 }
 
@@ -904,6 +909,10 @@ dkm_status apply_tuning(dkm_ctx* c, const dkm_tuning& t) {
     c->row_filter_min = t.row_filter_min;
     changed = true;
   }
+  if (t.sort_max != c->sort_max) {
+    c->sort_max = t.sort_max;
+    changed = true;
+  }
   if (changed) {
     destroy_graph(c);
     c->acc_valid = false;
@@ -917,6 +926,7 @@ dkm_tuning current_tuning(const dkm_ctx* c) {
   t.cells_per_centroid = c->cpc;
   t.tile_cut_div = c->cut_div;
   t.row_filter_min = c->row_filter_min;
+  t.sort_max = c->sort_max;
   return t;
 }
 
@@ -1017,6 +1027,12 @@ dkm_status autotune_impl(dkm_ctx* c, const float* init, int passes, int use_cach
     if (v == best.row_filter_min) continue;
     dkm_tuning t = best;
     t.row_filter_min = v;
+    DKM_TRY(trial(t));
+  }
+  for (int v : {0, 16, 32}) {
+    if (v == best.sort_max) continue;
+    dkm_tuning t = best;
+    t.sort_max = v;
     DKM_TRY(trial(t));
   }
   DKM_TRY(apply_tuning(c, best));

@@ -137,13 +137,14 @@ struct IterArgs {
   float4* gbkt[2];           // cells * cap entries
   float4* ovf[2];            // overflow lists: cloud b uses [c0, c0 + k)
   int* ovf_cnt[2];           // per cloud overflow count, two parities
-  int* tlist;                // n_tiles * kTileCap candidate ids (unordered)
+  float4* tlist;             // n_tiles * kTileCap candidates (x, y, z, id bits; unordered)
   int* tcnt;                 // per tile list length (> kTileCap = overflow)
   double* sse_hist;
   unsigned long long* chg_hist;
   int track_changes;         // read previous labels and count changes
   int early_stop;
   int row_filter_min;        // tile lists longer than this are filtered again per row
+  int sort_max;              // lists up to this length (<= 32) are sorted, early exit
 };
 
 // ---------------------------------------------------------------------------

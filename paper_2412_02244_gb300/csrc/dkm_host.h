@@ -83,6 +83,7 @@ struct dkm_ctx {
   std::vector<unsigned long long> h_level_hist;   // B x (kMaxLevels + 1)
   std::vector<float> h_blo, h_bhi;                // per-cloud point boxes (3 floats each)
   int row_filter_min = 48;     // per-row candidate filtering threshold
+  int sort_max = 0;            // sorted early-exit evaluation for lists up to this length
   bool ready = false;          // the point index is valid
   bool acc_valid = false;      // acc holds the sums of the last dkm_assign
 
@@ -115,7 +116,7 @@ struct dkm_ctx {
   float4* gbkt[2] = {nullptr, nullptr};
   float4* ovf[2] = {nullptr, nullptr};
   int* ovf_cnt[2] = {nullptr, nullptr};
-  int* tlist = nullptr;
+  float4* tlist = nullptr;     // per tile kTileCap candidates of the last search
   int* tcnt = nullptr;
   float* cstage = nullptr;     // k x d centroid staging
   float* cstage2 = nullptr;    // k x d centroid output staging

@@ -216,6 +216,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
 // of (d^2, id), which does not depend on the order.
 // ---------------------------------------------------------------------------
 constexpr int kSearchWarps = 2;   // independent warps: small CTAs free SM slots early
+#ifndef DKM_SEARCH_MIN_BLOCKS
+#define DKM_SEARCH_MIN_BLOCKS 24   // 40 registers: more resident warps hide the dependent loads
+#endif
 
 __device__ __forceinline__ long long cell_index(const Grid& G, int cx, int cy, int cz) {
   return ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
@@ -236,7 +239,8 @@ __device__ __forceinline__ void decode_cell(long long q, int nx, int ny, int& dx
 // MULTI = false: a single cloud, whose table entry is read from the kernel
 // parameters (constant bank) instead of global memory.
 template <bool MULTI>
-__global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_constant__ IterArgs A,
+__global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
+    k_search(const __grid_constant__ IterArgs A,
                                                                   int par, int d) {
   if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
   // clear the other parity's grids for the next rebuild (nobody reads them now)
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
   if (t >= A.n_tiles) return;
   const int b = MULTI ? A.tcloud[t] : 0;
   if (MULTI && A.crun[b].done) return;
-  int* __restrict__ out = A.tlist + (int64_t)t * kTileCap;
+  float4* __restrict__ out = A.tlist + (int64_t)t * kTileCap;
   const Cloud& cl = MULTI ? A.clouds[b] : A.cl0;
   const Grid G = cl.grid;
   const int c0 = cl.c0, c1 = cl.c0 + cl.k;
@@ -273,8 +277,22 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
   chi[2] = d == 3 ? cell_coord(hi.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
 
   // ---- phase A ----
+  // Any centroid of the cloud bounds the nearest distance of every point in
+  // the box by maxd(box, c).  The tile's list of the previous pass holds
+  // ids of this cloud near the tile (lists are cleared whenever the tiles
+  // change), so its current positions give U in one load round; without a
+  // list, rings of cells around the box are scanned.
   float u2 = INFINITY;
-  for (int ring = 0;; ring = ring ? 2 * ring : 1) {
+  const int q_old = A.tcnt[t];
+  if (q_old >= 1 && q_old <= kTileCap) {
+    float m = INFINITY;
+    for (int j = lane; j < q_old; j += 32) {
+      const float4 c = A.cw[__float_as_int(out[j].w)];
+      m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
+    }
+    u2 = warp_min_nonneg(m);   // every lane has read its old ids before any is overwritten
+  }
+  for (int ring = 0; !(u2 < INFINITY); ring = ring ? 2 * ring : 1) {
     int rlo[3], rhi[3];
     long long ncell = 1;
     bool whole = true;
@@ -299,13 +317,10 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
       decode_cell(q, nx, ny, ox, oy, oz);
       long long cell = cell_index(G, rlo[0] + ox, rlo[1] + oy, rlo[2] + oz);
       int cnt = min(gcnt[cell], kBucketCap);
-      float4 e[kBucketCap];
-#pragma unroll
-      for (int i = 0; i < kBucketCap; ++i)
-        if (i < cnt) e[i] = gbkt[cell * kBucketCap + i];
-#pragma unroll
-      for (int i = 0; i < kBucketCap; ++i)
-        if (i < cnt) m = fminf(m, maxd2(lo, hi, e[i].x, e[i].y, e[i].z, d));
+      for (int i = 0; i < cnt; ++i) {
+        const float4 e = gbkt[cell * kBucketCap + i];
+        m = fminf(m, maxd2(lo, hi, e.x, e.y, e.z, d));
+      }
     }
     for (int q = lane; q < n_ovf; q += 32) {
       float4 c = ovf[q];
@@ -350,7 +365,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
       }
       unsigned bal = __ballot_sync(0xffffffffu, keep);
       int pos = count + __popc(bal & lt);
-      if (keep && pos < kTileCap) out[pos] = __float_as_int(c.w);
+      if (keep && pos < kTileCap) out[pos] = c;
       count += __popc(bal);
     }
   } else {
@@ -364,18 +379,14 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
         cell = cell_index(G, rlo[0] + ox, rlo[1] + oy, rlo[2] + oz);
         cnt = min(gcnt[cell], kBucketCap);
       }
-      float4 e[kBucketCap];
-#pragma unroll
-      for (int i = 0; i < kBucketCap; ++i)
-        if (i < cnt) e[i] = gbkt[cell * kBucketCap + i];
       const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-#pragma unroll
-      for (int i = 0; i < kBucketCap; ++i) {
-        if (i >= cmax) break;
-        const bool keep = i < cnt && mind2(lo, hi, e[i].x, e[i].y, e[i].z, d) <= u2k;
+      for (int i = 0; i < cmax; ++i) {
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < cnt) e = gbkt[cell * kBucketCap + i];
+        const bool keep = i < cnt && mind2(lo, hi, e.x, e.y, e.z, d) <= u2k;
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         int pos = count + __popc(bal & lt);
-        if (keep && pos < kTileCap) out[pos] = __float_as_int(e[i].w);
+        if (keep && pos < kTileCap) out[pos] = e;
         count += __popc(bal);
       }
     }
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
       }
       unsigned bal = __ballot_sync(0xffffffffu, keep);
       int pos = count + __popc(bal & lt);
-      if (keep && pos < kTileCap) out[pos] = __float_as_int(c.w);
+      if (keep && pos < kTileCap) out[pos] = c;
       count += __popc(bal);
     }
   }
@@ -411,6 +422,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps, 12) k_search(const __grid_c
 #define DKM_ASSIGN_WARPS 2
 #endif
 constexpr int kAssignWarps = DKM_ASSIGN_WARPS;
+#ifndef DKM_ASSIGN_MIN_WARPS
+#define DKM_ASSIGN_MIN_WARPS 24
+#endif
 template <int D>
 struct Pts {
   float2 x[kRowsPerWarp], y[kRowsPerWarp], z[kRowsPerWarp];
@@ -528,13 +542,31 @@ __device__ __forceinline__ int filter_box(const float4* __restrict__ s_c, int m,
   return cnt;
 }
 
+__device__ __forceinline__ void add_group(const IterArgs& A, int D, int L, int sx, int sy, int sz,
+                                          int cnt, int s_q, int s_glob) {
+  Acc* a = &A.acc[L];
+  red_add_u64(&a->s[0], (unsigned long long)rescale(sx, s_q, s_glob));
+  red_add_u64(&a->s[1], (unsigned long long)rescale(sy, s_q, s_glob));
+  if (D == 3) red_add_u64(&a->s[2], (unsigned long long)rescale(sz, s_q, s_glob));
+  red_add_u64(&a->cnt, (unsigned long long)cnt);
+}
+
+// unit exponent s with n_max * max|r| * 2^s < 2^31 for groups of up to
+// 2^(31 - 1 - bits) points: 2^bits * max|r| * 2^s < 2^30
+__device__ __forceinline__ int group_scale(float m, int bits) {
+  return m > 0.f ? min(bits - exp_bound(m), 127) : 0;
+}
+
 // Tile epilogue shared by k_assign and k_accum_labels: residuals p - c of
-// all the tile's points (4 rows x 2 per lane) in 32-bit fixed point with
-// one tile-wide power-of-two scale (256 * max|r| * 2^s < 2^31, so int32
-// sums cannot overflow), grouped by label across the whole tile and added
-// to the per-centroid accumulators with 64-bit integer atomics.  The
-// grouping depends only on the tile and the labels, so every caller gets
-// the same sums bit for bit.
+// the tile's points (4 rows x 2 per lane) against their own centroid, in
+// 32-bit fixed point with one tile-wide power-of-two scale (256 points *
+// max|r| * 2^s < 2^31, so int32 sums cannot overflow), summed per label
+// and added to the per-centroid accumulators with 64-bit integer atomics.
+// A tile whose points all share one label loads its centroid once and adds
+// one group; otherwise every point loads its own centroid and the labels
+// are taken one at a time (the smallest pending label of the warp).  The
+// sums depend only on the tile and the labels, so every caller gets the
+// same sums bit for bit.
 template <int D>
 __device__ __forceinline__ void accumulate_tile(const IterArgs& A, const float2 (&px)[kRowsPerWarp],
                                                 const float2 (&py)[kRowsPerWarp],
@@ -542,72 +574,75 @@ __device__ __forceinline__ void accumulate_tile(const IterArgs& A, const float2 
                                                 const int2 (&lab)[kRowsPerWarp],
                                                 const bool (&va)[kRowsPerWarp],
                                                 const bool (&vb)[kRowsPerWarp], int s_glob) {
-  float rx[2 * kRowsPerWarp], ry[2 * kRowsPerWarp], rz[2 * kRowsPerWarp];
+  constexpr int H = 2 * kRowsPerWarp;
+  const int lane = threadIdx.x & 31;
+  int lb[H];
+  bool pend[H];
+  int lmin = INT_MAX;
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    lb[2 * r] = lab[r].x;
+    lb[2 * r + 1] = lab[r].y;
+    pend[2 * r] = va[r];
+    pend[2 * r + 1] = vb[r];
+  }
+#pragma unroll
+  for (int h = 0; h < H; ++h) lmin = pend[h] ? min(lmin, lb[h]) : lmin;
+  int L = __reduce_min_sync(0xffffffffu, lmin);
+  if (L == INT_MAX) return;   // no valid point
+  bool same = true;
+#pragma unroll
+  for (int h = 0; h < H; ++h) same = same && (!pend[h] || lb[h] == L);
+  const bool single = __all_sync(0xffffffffu, same);
+  float rx[H], ry[H], rz[H];
+  float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (single) c0 = __ldg(&A.cw[L]);
   float ml = 0.f;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    rx[2 * r] = ry[2 * r] = rz[2 * r] = 0.f;
-    rx[2 * r + 1] = ry[2 * r + 1] = rz[2 * r + 1] = 0.f;
-    if (va[r]) {
-      const float4 c = __ldg(&A.cw[lab[r].x]);
-      rx[2 * r] = __fadd_rn(px[r].x, -c.x);
-      ry[2 * r] = __fadd_rn(py[r].x, -c.y);
-      if (D == 3) rz[2 * r] = __fadd_rn(pz[r].x, -c.z);
-    }
-    if (vb[r]) {
-      const float4 c = __ldg(&A.cw[lab[r].y]);
-      rx[2 * r + 1] = __fadd_rn(px[r].y, -c.x);
-      ry[2 * r + 1] = __fadd_rn(py[r].y, -c.y);
-      if (D == 3) rz[2 * r + 1] = __fadd_rn(pz[r].y, -c.z);
-    }
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-      ml = fmaxf(ml, fmaxf(fmaxf(fabsf(rx[2 * r + h]), fabsf(ry[2 * r + h])), fabsf(rz[2 * r + h])));
+    for (int hh = 0; hh < 2; ++hh) {
+      const int h = 2 * r + hh;
+      rx[h] = ry[h] = rz[h] = 0.f;
+      if (pend[h]) {
+        const float4 c = single ? c0 : __ldg(&A.cw[lb[h]]);
+        rx[h] = __fadd_rn(hh ? px[r].y : px[r].x, -c.x);
+        ry[h] = __fadd_rn(hh ? py[r].y : py[r].x, -c.y);
+        if (D == 3) rz[h] = __fadd_rn(hh ? pz[r].y : pz[r].x, -c.z);
+      }
+      ml = fmaxf(ml, fmaxf(fmaxf(fabsf(rx[h]), fabsf(ry[h])), fabsf(rz[h])));
+    }
   }
-  const float m = warp_max_nonneg(ml);
-  const int s_t = m > 0.f ? min(22 - exp_bound(m), 127) : 0;
+  const int s_t = group_scale(warp_max_nonneg(ml), 22);
   const float sc = pow2f(s_t);
-  int qx[2 * kRowsPerWarp], qy[2 * kRowsPerWarp], qz[2 * kRowsPerWarp], lb[2 * kRowsPerWarp];
-  bool pend[2 * kRowsPerWarp];
+  int qx[H], qy[H], qz[H];
 #pragma unroll
-  for (int h = 0; h < 2 * kRowsPerWarp; ++h) {
+  for (int h = 0; h < H; ++h) {
     qx[h] = __float2int_rn(rx[h] * sc);
     qy[h] = __float2int_rn(ry[h] * sc);
     qz[h] = D == 3 ? __float2int_rn(rz[h] * sc) : 0;
-    lb[h] = (h & 1) ? lab[h >> 1].y : lab[h >> 1].x;
-    pend[h] = (h & 1) ? vb[h >> 1] : va[h >> 1];
   }
-  const int lane = threadIdx.x & 31;
   while (true) {
-    // label of the first pending point (slot-major, then lane)
-    int L = -1;
-#pragma unroll
-    for (int h = 0; h < 2 * kRowsPerWarp; ++h) {
-      const unsigned mk = __ballot_sync(0xffffffffu, pend[h]);
-      if (L < 0 && mk) L = __shfl_sync(0xffffffffu, lb[h], __ffs(mk) - 1);
-    }
-    if (L < 0) break;
     int sx = 0, sy = 0, sz = 0, cnt = 0;
+    lmin = INT_MAX;
 #pragma unroll
-    for (int h = 0; h < 2 * kRowsPerWarp; ++h) {
+    for (int h = 0; h < H; ++h) {
       const bool g = pend[h] && lb[h] == L;
       sx += g ? qx[h] : 0;
       sy += g ? qy[h] : 0;
       sz += g ? qz[h] : 0;
       cnt += g ? 1 : 0;
       pend[h] = pend[h] && !g;
+      lmin = pend[h] ? min(lmin, lb[h]) : lmin;
     }
     sx = __reduce_add_sync(0xffffffffu, sx);
     sy = __reduce_add_sync(0xffffffffu, sy);
     if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if (lane == 0) {
-      Acc* a = &A.acc[L];
-      red_add_u64(&a->s[0], (unsigned long long)rescale(sx, s_t, s_glob));
-      red_add_u64(&a->s[1], (unsigned long long)rescale(sy, s_t, s_glob));
-      if (D == 3) red_add_u64(&a->s[2], (unsigned long long)rescale(sz, s_t, s_glob));
-      red_add_u64(&a->cnt, (unsigned long long)cnt);
-    }
+    if (lane == 0) add_group(A, D, L, sx, sy, sz, cnt, s_t, s_glob);
+    if (single) break;
+    L = __reduce_min_sync(0xffffffffu, lmin);
+    if (L == INT_MAX) break;
   }
 }
 
@@ -651,7 +686,7 @@ __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t ba
 }
 
 template <int D, bool BRUTE, bool MULTI>
-__global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2)
+__global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAssignWarps)
     k_assign(const __grid_constant__ IterArgs A) {
   __shared__ float4 s_c[kAssignWarps][kTileCap];
   __shared__ unsigned short s_r[kAssignWarps][kTileCap];
@@ -698,16 +733,15 @@ __global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2)
     evals = (unsigned long long)cl.k * nv_tile;
   } else {
     const int q = A.tcnt[t];
-    if (q <= 32) {
+    if (q == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
+    if (q <= A.sort_max) {   // sort_max <= 32
       // Short list: order it by the lower bound mind^2(tile box, c) and stop
       // once the next bound exceeds every point's current best (the kNN
       // pruning rule of Algorithm 1's kNN function, with the tile box as
       // the query node).  (d^2, id) keys make the result order independent.
-      if (q == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
       const float4 tlo = A.tbox[2 * t], thi = A.tbox[2 * t + 1];
       const bool has = lane < q;
-      const float4 c = has ? __ldg(&A.cw[A.tlist[(int64_t)t * kTileCap + lane]])
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 c = has ? A.tlist[(int64_t)t * kTileCap + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float lb = has ? mind2(tlo, thi, c.x, c.y, c.z, D) : INFINITY;
       const unsigned long long key =
           ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)lane;
@@ -733,8 +767,8 @@ __global__ void __launch_bounds__(32 * kAssignWarps, 12 / kAssignWarps * 2)
       }
       evals = (unsigned long long)done * nv_tile;
     } else if (q <= kTileCap) {
-      const int* src = A.tlist + (int64_t)t * kTileCap;
-      for (int i = lane; i < q; i += 32) sc[i] = __ldg(&A.cw[src[i]]);
+      const float4* src = A.tlist + (int64_t)t * kTileCap;
+      for (int i = lane; i < q; i += 32) sc[i] = src[i];
       __syncwarp();
       if (q > A.row_filter_min) {
         // long list: narrow it again per row of 64 points
