@@ -265,6 +265,11 @@ typedef struct {
      * lower bound and evaluated with an early exit once the bound exceeds
      * every point's current best (the kNN pruning rule); default 0 (off) */
     int sort_max;
+    /* hierarchical tiles: groups of this many consecutive tiles of a cloud
+     * share one candidate search over the union of their boxes, and each
+     * tile narrows the group's list with its own box; 1 .. 32, default 1
+     * (every tile searches on its own) */
+    int tile_group;
     /* dkm_autotune only: mean ms per Lloyd pass of the chosen setting and
      * of the setting the context had before, configurations timed, and
      * whether the choice came from the process-wide cache (nothing timed) */
@@ -284,8 +289,8 @@ DKM_API dkm_status dkm_set_tuning(dkm_ctx* ctx, const dkm_tuning* tuning);
 /*
  * Measure and apply the fastest setting for this context: coordinate
  * descent over cells_per_centroid {0.5, 1, 2, 4}, tile_cut_div
- * {2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256} and sort_max
- * {0, 16, 32}, each
+ * {2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256}, sort_max
+ * {0, 16, 32} and tile_group {1, 2, 4, 8, 16}, each
  * setting timed (CUDA events, best of two) over `passes` Lloyd passes
  * (1 .. 64, no early stop) from init_centroids.  The context's labels and
  * centroids are overwritten by those runs.  With use_cache = 1 a setting

@@ -167,7 +167,7 @@ struct Layout {
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
   size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles,
-      tcloud, kcloud, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+      tcloud, kcloud, ubox, ucloud, ufirst, tunit, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
 };
@@ -200,6 +200,10 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.n_tiles = L.take<int>(1);
   P.tcloud = L.take<int>(tm);
   P.kcloud = L.take<int>(k);
+  P.ubox = L.take<float4>(2 * tm);
+  P.ucloud = L.take<int>(tm);
+  P.ufirst = L.take<int>(tm + 1);
+  P.tunit = L.take<int>(tm);
   P.wcnt = L.take<int>(nw);
   P.wbase = L.take<int>(nw);
   P.level_hist = L.take<unsigned long long>(B * (kMaxLevels + 1));
@@ -249,6 +253,11 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.tiles = c->tiles;
   A.tcloud = c->tcloud;
   A.kcloud = c->kcloud;
+  A.unit_g = c->unit_g;
+  A.n_units = c->n_units;
+  A.ubox = c->unit_g > 1 ? c->ubox : c->tbox;
+  A.ucloud = c->unit_g > 1 ? c->ucloud : c->tcloud;
+  A.tunit = c->tunit;
   A.clouds = c->clouds;
   A.cl0 = c->h_clouds[0];
   A.crun = c->crun;
@@ -561,6 +570,8 @@ dkm_status plan_clouds(dkm_ctx* c, const std::vector<float>& blo, const std::vec
   return DKM_OK;
 }
 
+dkm_status apply_units(dkm_ctx* c);
+
 // Tiles from the level histogram: per cloud the finest Morton level whose
 // cubes cut its sorted run into at most max(1, windows_b / cut_div) pieces
 // (so cube cuts add few tiles), then tile ranges, boxes and the tile ->
@@ -597,6 +608,34 @@ dkm_status apply_tiling(dkm_ctx* c) {
   // the kernel filled each cloud's first tile: refresh the host copy
   DKM_CK(cudaMemcpyAsync(c->h_clouds.data(), c->clouds, sizeof(Cloud) * c->B,
                          cudaMemcpyDeviceToHost, c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  return apply_units(c);
+}
+
+// Search units (hierarchical tiles): groups of unit_g consecutive tiles of
+// one cloud share one grid search over the union of their boxes, and each
+// tile narrows the unit's list with its own box in k_assign.  unit_g = 1:
+// every tile is its own unit.
+dkm_status apply_units(dkm_ctx* c) {
+  destroy_graph(c);
+  DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
+  if (c->unit_g <= 1) {
+    c->n_units = c->n_tiles;
+    return DKM_OK;
+  }
+  std::vector<int> uf;
+  uf.reserve((size_t)c->n_tiles / c->unit_g + c->B + 1);
+  for (int b = 0; b < c->B; ++b) {
+    const int t_begin = c->h_clouds[b].t0;
+    const int t_end = b + 1 < c->B ? c->h_clouds[b + 1].t0 : c->n_tiles;
+    for (int t = t_begin; t < t_end; t += c->unit_g) uf.push_back(t);
+  }
+  uf.push_back(c->n_tiles);
+  c->n_units = (int)uf.size() - 1;
+  DKM_CK(cudaMemcpyAsync(c->ufirst, uf.data(), sizeof(int) * uf.size(), cudaMemcpyHostToDevice,
+                         c->stream));
+  DKM_CK(launch_unit_boxes(c->tbox, c->tcloud, c->ufirst, c->n_units, c->ubox, c->ucloud,
+                           c->tunit, c->stream));
   DKM_CK(cudaStreamSynchronize(c->stream));
   return DKM_OK;
 }
@@ -748,6 +787,10 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->n_tiles_dev = (int*)(base + P.n_tiles);
   c->tcloud = (int*)(base + P.tcloud);
   c->kcloud = (int*)(base + P.kcloud);
+  c->ubox = (float4*)(base + P.ubox);
+  c->ucloud = (int*)(base + P.ucloud);
+  c->ufirst = (int*)(base + P.ufirst);
+  c->tunit = (int*)(base + P.tunit);
   c->wcnt = (int*)(base + P.wcnt);
   c->wbase = (int*)(base + P.wbase);
   c->level_hist = (unsigned long long*)(base + P.level_hist);
@@ -888,6 +931,8 @@ dkm_status tuning_check(const dkm_ctx* c, const dkm_tuning& t) {
   if (t.row_filter_min < 0) return fail(DKM_EINVAL, "row_filter_min must be >= 0");
   if (t.sort_max < 0 || t.sort_max > 32)
     return fail(DKM_EINVAL, "sort_max must be in [0, 32] (got %d)", t.sort_max);
+  if (t.tile_group < 1 || t.tile_group > 32)
+    return fail(DKM_EINVAL, "tile_group must be in [1, 32] (got %d)", t.tile_group);
   return DKM_OK;
 }
 
@@ -913,6 +958,11 @@ dkm_status apply_tuning(dkm_ctx* c, const dkm_tuning& t) {
     c->sort_max = t.sort_max;
     changed = true;
   }
+  if (t.tile_group != c->unit_g) {
+    c->unit_g = t.tile_group;
+    DKM_TRY(apply_units(c));
+    changed = true;
+  }
   if (changed) {
     destroy_graph(c);
     c->acc_valid = false;
@@ -927,6 +977,7 @@ dkm_tuning current_tuning(const dkm_ctx* c) {
   t.tile_cut_div = c->cut_div;
   t.row_filter_min = c->row_filter_min;
   t.sort_max = c->sort_max;
+  t.tile_group = c->unit_g;
   return t;
 }
 
@@ -1033,6 +1084,12 @@ dkm_status autotune_impl(dkm_ctx* c, const float* init, int passes, int use_cach
     if (v == best.sort_max) continue;
     dkm_tuning t = best;
     t.sort_max = v;
+    DKM_TRY(trial(t));
+  }
+  for (int v : {1, 2, 4, 8, 16}) {
+    if (v == best.tile_group) continue;
+    dkm_tuning t = best;
+    t.tile_group = v;
     DKM_TRY(trial(t));
   }
   DKM_TRY(apply_tuning(c, best));

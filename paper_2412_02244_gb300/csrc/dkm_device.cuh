@@ -120,6 +120,13 @@ struct IterArgs {
   int n_tiles;               // tiles of the point index (launch size)
   const int2* tiles;         // per tile: [start, end) in sorted order
   const int* tcloud;         // per tile: its cloud
+  // Search units: tile_group consecutive tiles of one cloud share one grid
+  // search (unit_g = 1: every tile is its own unit, ubox = tbox).
+  int unit_g;
+  int n_units;
+  const float4* ubox;        // per unit: lo, hi
+  const int* ucloud;         // per unit: its cloud
+  const int* tunit;          // per tile: its unit (unit_g > 1)
   const int* kcloud;         // per centroid: its cloud
   const Cloud* clouds;
   Cloud cl0;                 // copy of clouds[0] (kernel-parameter space)
@@ -137,8 +144,8 @@ struct IterArgs {
   float4* gbkt[2];           // cells * cap entries
   float4* ovf[2];            // overflow lists: cloud b uses [c0, c0 + k)
   int* ovf_cnt[2];           // per cloud overflow count, two parities
-  float4* tlist;             // n_tiles * kTileCap candidates (x, y, z, id bits; unordered)
-  int* tcnt;                 // per tile list length (> kTileCap = overflow)
+  float4* tlist;             // per unit kTileCap candidates (x, y, z, id bits; unordered)
+  int* tcnt;                 // per unit list length (> kTileCap = overflow)
   double* sse_hist;
   unsigned long long* chg_hist;
   int track_changes;         // read previous labels and count changes

@@ -45,6 +45,9 @@ cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
 cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int32_t* labels_out,
                             int do_sse, cudaStream_t s);
 cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s);
+cudaError_t launch_unit_boxes(const float4* tbox, const int* tcloud, const int* ufirst,
+                              int n_units, float4* ubox, int* ucloud, int* tunit,
+                              cudaStream_t s);
 
 // dkm_api.cu: set the calling thread's dkm_last_error() message
 void dkm_set_last_error(const char* msg);
@@ -74,6 +77,8 @@ struct dkm_ctx {
   int n_tiles = 0;             // tiles of the current point index
   int tile_level = 0;          // Morton level whose cube boundaries cut cloud 0's tiles
   int cut_div = 8;             // cube cuts may add n_windows / cut_div tiles per cloud
+  int unit_g = 1;              // tiles per search unit
+  int n_units = 0;             // search units of the current tiling
   float cpc = 1.0f;            // grid cells per centroid (before the budget cap)
   int64_t n_pad = 0;
   int64_t max_cells = 0;       // grid capacity the arena was sized for
@@ -101,6 +106,8 @@ struct dkm_ctx {
   int* n_tiles_dev = nullptr;
   int* tcloud = nullptr;
   int* kcloud = nullptr;
+  float4* ubox = nullptr;      // per unit box (unit_g > 1)
+  int *ucloud = nullptr, *ufirst = nullptr, *tunit = nullptr;
   int *wcnt = nullptr, *wbase = nullptr;
   unsigned long long* level_hist = nullptr;
   int64_t *doff = nullptr, *dcoff = nullptr;

@@ -236,30 +236,28 @@ __device__ __forceinline__ void decode_cell(long long q, int nx, int ny, int& dx
   dz = (int)z;
 }
 
+// clear the other parity's grids for the next rebuild (nobody reads them
+// during this pass)
+__device__ __forceinline__ void clear_other_parity(const IterArgs& A, int par) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = g; c < A.total_cells; c += stride) A.gcnt[par ^ 1][c] = 0;
+  for (long long c = g; c < A.B; c += stride) A.ovf_cnt[par ^ 1][c] = 0;
+}
+
+// The candidate search of search unit t (one warp), list to tlist / tcnt.
 // MULTI = false: a single cloud, whose table entry is read from the kernel
 // parameters (constant bank) instead of global memory.
 template <bool MULTI>
-__global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
-    k_search(const __grid_constant__ IterArgs A,
-                                                                  int par, int d) {
-  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
-  // clear the other parity's grids for the next rebuild (nobody reads them now)
-  {
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c = g; c < A.total_cells; c += stride) A.gcnt[par ^ 1][c] = 0;
-    for (long long c = g; c < A.B; c += stride) A.ovf_cnt[par ^ 1][c] = 0;
-  }
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int t = blockIdx.x * kSearchWarps + wl;
-  if (t >= A.n_tiles) return;
-  const int b = MULTI ? A.tcloud[t] : 0;
+__device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, int t) {
+  const int lane = threadIdx.x & 31;
+  const int b = MULTI ? A.ucloud[t] : 0;
   if (MULTI && A.crun[b].done) return;
   float4* __restrict__ out = A.tlist + (int64_t)t * kTileCap;
   const Cloud& cl = MULTI ? A.clouds[b] : A.cl0;
   const Grid G = cl.grid;
   const int c0 = cl.c0, c1 = cl.c0 + cl.k;
-  const float4 lo = A.tbox[2 * t], hi = A.tbox[2 * t + 1];
+  const float4 lo = A.ubox[2 * t], hi = A.ubox[2 * t + 1];
   const int* __restrict__ gcnt = A.gcnt[par] + cl.cell0;
   const float4* __restrict__ gbkt = A.gbkt[par] + cl.cell0 * kBucketCap;
   const int n_ovf = A.ovf_cnt[par][b];
@@ -412,6 +410,16 @@ __global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
   }
 }
 
+template <bool MULTI>
+__global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
+    k_search(const __grid_constant__ IterArgs A, int par, int d) {
+  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
+  clear_other_parity(A, par);
+  const int t = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
+  if (t >= A.n_units) return;   // t: the search unit (a tile or a group of tiles)
+  search_unit<MULTI>(A, par, d, t);
+}
+
 // ---------------------------------------------------------------------------
 // k_assign<D, BRUTE>: one warp per tile of 4 rows x 64 points, two points
 // per lane evaluated as packed f32x2.  Warps are independent (no CTA-wide
@@ -557,6 +565,39 @@ __device__ __forceinline__ int group_scale(float m, int bits) {
   return m > 0.f ? min(bits - exp_bound(m), 127) : 0;
 }
 
+// The entries of src[0..m) (global memory) that can hold the nearest
+// centroid of some point inside [lo, hi], written compactly to out (shared
+// memory, m <= kTileCap); returns the count.  U = min over the list of
+// maxd(box, c) bounds every point's nearest distance (any centroid of the
+// cloud does), and a point's nearest centroid c* has mind(box, c*) <= U.
+template <int D>
+__device__ __forceinline__ int filter_list(const float4* __restrict__ src, int m, float4 lo,
+                                           float4 hi, float4* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  float u = INFINITY;
+  for (int j = lane; j < m; j += 32) {
+    const float4 c = src[j];
+    u = fminf(u, maxd2(lo, hi, c.x, c.y, c.z, D));
+  }
+  const float u2k = warp_min_nonneg(u) * kKeep;
+  const unsigned lt = (1u << lane) - 1u;
+  int cnt = 0;
+  for (int j0 = 0; j0 < m; j0 += 32) {
+    const int j = j0 + lane;
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool keep = false;
+    if (j < m) {
+      c = src[j];
+      keep = mind2(lo, hi, c.x, c.y, c.z, D) <= u2k;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) out[cnt + __popc(bal & lt)] = c;
+    cnt += __popc(bal);
+  }
+  __syncwarp();
+  return cnt;
+}
+
 // Tile epilogue shared by k_assign and k_accum_labels: residuals p - c of
 // the tile's points (4 rows x 2 per lane) against their own centroid, in
 // 32-bit fixed point with one tile-wide power-of-two scale (256 points *
@@ -685,16 +726,14 @@ __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t ba
   }
 }
 
-template <int D, bool BRUTE, bool MULTI>
-__global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAssignWarps)
-    k_assign(const __grid_constant__ IterArgs A) {
-  __shared__ float4 s_c[kAssignWarps][kTileCap];
-  __shared__ unsigned short s_r[kAssignWarps][kTileCap];
-  __shared__ float slb[kAssignWarps][32];
-  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int t = blockIdx.x * kAssignWarps + w;
-  if (t >= A.n_tiles) return;   // warp-level exits, no CTA barrier below
+// Assignment of tile t (one warp) from its search unit's candidate list:
+// labels, SSE and the update sums.  sc / sr / slbw: the warp's shared
+// staging (kTileCap candidates, kTileCap indices, 32 bounds).
+template <int D, bool BRUTE, bool MULTI, bool UNITS>
+__device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __restrict__ sc,
+                                            unsigned short* __restrict__ sr,
+                                            float* __restrict__ slbw) {
+  const int lane = threadIdx.x & 31;
   const int b = MULTI ? A.tcloud[t] : 0;
   if (MULTI && A.crun[b].done) return;
   const Cloud& cl = MULTI ? A.clouds[b] : A.cl0;
@@ -720,8 +759,6 @@ __global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAss
     bid[r] = make_int2(0, 0);
   }
   unsigned long long evals = 0;   // point x candidate evaluations of this warp
-  float4* __restrict__ sc = s_c[w];
-  unsigned short* __restrict__ sr = s_r[w];
   if (BRUTE) {
     for (int j0 = c0; j0 < c1; j0 += kTileCap) {
       const int m = min(kTileCap, c1 - j0);
@@ -732,45 +769,54 @@ __global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAss
     }
     evals = (unsigned long long)cl.k * nv_tile;
   } else {
-    const int q = A.tcnt[t];
-    if (q == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
-    if (q <= A.sort_max) {   // sort_max <= 32
-      // Short list: order it by the lower bound mind^2(tile box, c) and stop
-      // once the next bound exceeds every point's current best (the kNN
-      // pruning rule of Algorithm 1's kNN function, with the tile box as
-      // the query node).  (d^2, id) keys make the result order independent.
-      const float4 tlo = A.tbox[2 * t], thi = A.tbox[2 * t + 1];
-      const bool has = lane < q;
-      const float4 c = has ? A.tlist[(int64_t)t * kTileCap + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float lb = has ? mind2(tlo, thi, c.x, c.y, c.z, D) : INFINITY;
-      const unsigned long long key =
-          ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)lane;
-      int rank = 0;
-      for (int m = 0; m < q; ++m) rank += __shfl_sync(0xffffffffu, key, m) < key;
-      if (has) {
-        sc[rank] = c;
-        slb[w][rank] = lb;
+    const int u = UNITS ? A.tunit[t] : t;   // the tile's search unit
+    const int qs = A.tcnt[u];
+    if (qs == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
+    if (qs <= kTileCap) {
+      const float4* __restrict__ src = A.tlist + (int64_t)u * kTileCap;
+      int q = qs;
+      if (UNITS) {
+        // the unit's list holds every candidate of the group's box; narrow
+        // it with this tile's own box (the bound of k_search)
+        q = filter_list<D>(src, qs, A.tbox[2 * t], A.tbox[2 * t + 1], sc);
+      } else {
+        for (int i = lane; i < qs; i += 32) sc[i] = src[i];
+        __syncwarp();
       }
-      __syncwarp();
-      int done = 0;
-      for (int j0 = 0; j0 < q; j0 += 4) {
-        if (j0 > 0) {
-          float mb = 0.f;
-#pragma unroll
-          for (int r = 0; r < kRowsPerWarp; ++r)
-            mb = fmaxf(mb, fmaxf(va[r] ? best[r].x : 0.f, vb[r] ? best[r].y : 0.f));
-          if (slb[w][j0] > warp_max_nonneg(mb) * kKeep) break;
+      if (q <= A.sort_max) {   // sort_max <= 32
+        // Short list: order it by the lower bound mind^2(tile box, c) and
+        // stop once the next bound exceeds every point's current best (the
+        // kNN pruning rule of Algorithm 1's kNN function, with the tile box
+        // as the query node).  (d^2, id) keys make the result order
+        // independent.
+        const float4 tlo = A.tbox[2 * t], thi = A.tbox[2 * t + 1];
+        const bool has = lane < q;
+        const float4 c = has ? sc[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float lb = has ? mind2(tlo, thi, c.x, c.y, c.z, D) : INFINITY;
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)lane;
+        int rank = 0;
+        for (int m = 0; m < q; ++m) rank += __shfl_sync(0xffffffffu, key, m) < key;
+        if (has) {
+          sr[rank] = (unsigned short)lane;
+          slbw[rank] = lb;
         }
-        const int m = min(4, q - j0);
-        eval_list<D>(sc + j0, nullptr, m, P, best, bid);
-        done = j0 + m;
-      }
-      evals = (unsigned long long)done * nv_tile;
-    } else if (q <= kTileCap) {
-      const float4* src = A.tlist + (int64_t)t * kTileCap;
-      for (int i = lane; i < q; i += 32) sc[i] = src[i];
-      __syncwarp();
-      if (q > A.row_filter_min) {
+        __syncwarp();
+        int done = 0;
+        for (int j0 = 0; j0 < q; j0 += 4) {
+          if (j0 > 0) {
+            float mb = 0.f;
+#pragma unroll
+            for (int r = 0; r < kRowsPerWarp; ++r)
+              mb = fmaxf(mb, fmaxf(va[r] ? best[r].x : 0.f, vb[r] ? best[r].y : 0.f));
+            if (slbw[j0] > warp_max_nonneg(mb) * kKeep) break;
+          }
+          const int m = min(4, q - j0);
+          eval_list<D>(sc, sr + j0, m, P, best, bid);
+          done = j0 + m;
+        }
+        evals = (unsigned long long)done * nv_tile;
+      } else if (q > A.row_filter_min) {
         // long list: narrow it again per row of 64 points
 #pragma unroll
         for (int r = 0; r < kRowsPerWarp; ++r) {
@@ -854,6 +900,22 @@ __global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAss
     if (changed) red_add_u64(&ca.changed[t & (kCloudSlots - 1)], (unsigned long long)changed);
     red_add_u64(&A.slots[t & (kSlots - 1)].evals, evals);
   }
+}
+
+
+// UNITS: tiles share search units (tile_group > 1) and filter their unit's
+// list with their own box.
+template <int D, bool BRUTE, bool MULTI, bool UNITS>
+__global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAssignWarps)
+    k_assign(const __grid_constant__ IterArgs A) {
+  __shared__ float4 s_c[kAssignWarps][kTileCap];
+  __shared__ unsigned short s_r[kAssignWarps][kTileCap];
+  __shared__ float slb[kAssignWarps][32];
+  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
+  const int w = threadIdx.x >> 5;
+  const int t = blockIdx.x * kAssignWarps + w;
+  if (t >= A.n_tiles) return;   // warp-level exits, no CTA barrier below
+  assign_tile<D, BRUTE, MULTI, UNITS>(A, t, s_c[w], s_r[w], slb[w]);
 }
 
 // ---------------------------------------------------------------------------
@@ -967,7 +1029,7 @@ cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const fl
 }
 
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
-  const int g = ceil_div(A.n_tiles, kSearchWarps);
+  const int g = ceil_div(A.n_units, kSearchWarps);
   if (A.B > 1) k_search<true><<<g, 32 * kSearchWarps, 0, s>>>(A, par, d);
   else k_search<false><<<g, 32 * kSearchWarps, 0, s>>>(A, par, d);
   return cudaGetLastError();
@@ -976,8 +1038,13 @@ cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
 template <int D, bool BRUTE>
 void assign_multi(const IterArgs& A, int g, cudaStream_t s) {
   constexpr int thr = 32 * kAssignWarps;
-  if (A.B > 1) k_assign<D, BRUTE, true><<<g, thr, 0, s>>>(A);
-  else k_assign<D, BRUTE, false><<<g, thr, 0, s>>>(A);
+  if (!BRUTE && A.unit_g > 1) {
+    if (A.B > 1) k_assign<D, false, true, true><<<g, thr, 0, s>>>(A);
+    else k_assign<D, false, false, true><<<g, thr, 0, s>>>(A);
+    return;
+  }
+  if (A.B > 1) k_assign<D, BRUTE, true, false><<<g, thr, 0, s>>>(A);
+  else k_assign<D, BRUTE, false, false><<<g, thr, 0, s>>>(A);
 }
 
 cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s) {
@@ -1015,6 +1082,50 @@ cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int3
 
 cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s) {
   k_export<<<ceil_div(k, 256), 256, 0, s>>>(cw, k, d, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Search units of tile_group > 1: unit u covers tiles [ufirst[u],
+// ufirst[u+1]) of one cloud (at most 32); its box is the union of theirs.
+// One warp per unit.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) k_unit_boxes(const float4* __restrict__ tbox,
+                                                              const int* __restrict__ tcloud,
+                                                              const int* __restrict__ ufirst,
+                                                              int n_units, float4* __restrict__ ubox,
+                                                              int* __restrict__ ucloud,
+                                                              int* __restrict__ tunit) {
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (u >= n_units) return;
+  const int f = ufirst[u], cnt = ufirst[u + 1] - f;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  if (lane < cnt) {
+    const float4 a = tbox[2 * (f + lane)], z = tbox[2 * (f + lane) + 1];
+    lo[0] = a.x; lo[1] = a.y; lo[2] = a.z;
+    hi[0] = z.x; hi[1] = z.y; hi[2] = z.z;
+    tunit[f + lane] = u;
+  }
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if (lane == 0) {
+    ubox[2 * u] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    ubox[2 * u + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    ucloud[u] = tcloud[f];
+  }
+}
+
+cudaError_t launch_unit_boxes(const float4* tbox, const int* tcloud, const int* ufirst,
+                              int n_units, float4* ubox, int* ucloud, int* tunit,
+                              cudaStream_t s) {
+  k_unit_boxes<<<ceil_div(n_units, kWarpsPerBlock), kBlockThreads, 0, s>>>(tbox, tcloud, ufirst,
+                                                                          n_units, ubox, ucloud,
+                                                                          tunit);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ class dkm_stats(ctypes.Structure):
 class dkm_tuning(ctypes.Structure):
     _fields_ = [("cells_per_centroid", ctypes.c_float), ("tile_cut_div", ctypes.c_int),
                 ("row_filter_min", ctypes.c_int), ("sort_max", ctypes.c_int),
+                ("tile_group", ctypes.c_int),
                 ("ms_per_pass", ctypes.c_float),
                 ("ms_per_pass_before", ctypes.c_float), ("trials", ctypes.c_int),
                 ("from_cache", ctypes.c_int)]
