@@ -263,10 +263,13 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
                                   "unit": "GB/s", "frac": achieved / hbm},
             "tuning": {"cells_per_centroid": tune.cells_per_centroid,
                        "tile_cut_div": tune.tile_cut_div, "row_filter_min": tune.row_filter_min,
+                       "sort_max": tune.sort_max, "tile_group": tune.tile_group,
+                       "stay_test": tune.stay_test,
                        "ms_per_pass": tune.ms_per_pass,
                        "ms_per_pass_default": tune.ms_per_pass_before, "trials": tune.trials},
             "pruning": {"evals_per_point": st.evals_per_point,
-                        "candidates_per_tile": st.candidates_per_tile, "tiles": st.tiles},
+                        "candidates_per_tile": st.candidates_per_tile, "tiles": st.tiles,
+                        "stayed_tiles": st.stayed_tiles},
             "brute_force": {"ms_per_pass": per_b, "indexed_ms_per_pass": per_i,
                             "speedup_indexed_over_brute": per_b / per_i if per_i > 0 else None,
                             "from": "final centroids of the timed run, 2 passes each"},
@@ -455,6 +458,7 @@ def run_ours(args):
     line["pruning"] = {"evals_per_point": stats.evals_per_point,
                        "candidates_per_tile": stats.candidates_per_tile,
                        "fallback_tiles": stats.fallback_tiles,
+                       "stayed_tiles": stats.stayed_tiles,
                        "tiles": stats.tiles, "tile_level": stats.tile_level,
                        "grid_overflow": stats.grid_overflow}
     if brute:

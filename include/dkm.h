@@ -111,6 +111,7 @@ typedef struct {
     double evals_per_point;     /* candidate distance evaluations per point, last pass */
     double candidates_per_tile; /* mean tile candidate-list length, last pass */
     int64_t fallback_tiles;     /* tiles whose candidate list overflowed, last pass */
+    int64_t stayed_tiles;       /* tiles that passed the stay test, last pass */
     int64_t grid_overflow;      /* centroids placed in the overflow list, last rebuild */
     int64_t tiles;              /* tiles of the point index (<= 256 points each) */
     int tile_level;             /* Morton level whose cubes bound the tiles */
@@ -270,6 +271,13 @@ typedef struct {
      * tile narrows the group's list with its own box; 1 .. 32, default 1
      * (every tile searches on its own) */
     int tile_group;
+    /* the bound layer (Section IV-A): 1 = before searching, a tile whose
+     * points all had label a in the last pass keeps a for every point when
+     * its box lies within half the distance from c_a to the nearest other
+     * centroid (maxd(box, c_a) < cb[a] / 2, cb from a grid kNN(2) over
+     * the centroids after each update); such a tile skips the grid search.
+     * Only with tile_group = 1; default 0 */
+    int stay_test;
     /* dkm_autotune only: mean ms per Lloyd pass of the chosen setting and
      * of the setting the context had before, configurations timed, and
      * whether the choice came from the process-wide cache (nothing timed) */
@@ -290,7 +298,7 @@ DKM_API dkm_status dkm_set_tuning(dkm_ctx* ctx, const dkm_tuning* tuning);
  * Measure and apply the fastest setting for this context: coordinate
  * descent over cells_per_centroid {0.5, 1, 2, 4}, tile_cut_div
  * {2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256}, sort_max
- * {0, 16, 32} and tile_group {1, 2, 4, 8, 16}, each
+ * {0, 16, 32}, tile_group {1, 2, 4, 8, 16} and stay_test {0, 1}, each
  * setting timed (CUDA events, best of two) over `passes` Lloyd passes
  * (1 .. 64, no early stop) from init_centroids.  The context's labels and
  * centroids are overwritten by those runs.  With use_cache = 1 a setting

@@ -167,7 +167,7 @@ struct Layout {
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
   size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles,
-      tcloud, kcloud, ubox, ucloud, ufirst, tunit, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+      tcloud, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
 };
@@ -204,6 +204,8 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.ucloud = L.take<int>(tm);
   P.ufirst = L.take<int>(tm + 1);
   P.tunit = L.take<int>(tm);
+  P.cb2 = L.take<float>(k);
+  P.tlab = L.take<int>(tm);
   P.wcnt = L.take<int>(nw);
   P.wbase = L.take<int>(nw);
   P.level_hist = L.take<unsigned long long>(B * (kMaxLevels + 1));
@@ -286,6 +288,9 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.early_stop = early_stop;
   A.row_filter_min = c->row_filter_min;
   A.sort_max = c->sort_max;
+  A.stay = (c->stay && c->unit_g == 1 && c->opts.algo != DKM_ALGO_BRUTE) ? 1 : 0;
+  A.cb2 = c->cb2;
+  A.tlab = c->tlab;
   return A;
 }
 
@@ -406,6 +411,7 @@ dkm_status one_pass(dkm_ctx* c, bool track_changes) {
   DKM_TRY(zero_run_buffers(c, false));
   IterArgs A = iter_args(c, track_changes ? 1 : 0, 0);
   DKM_CK(launch_centroids(A, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream));
+  if (A.stay) DKM_CK(launch_cbound(A, 0, c->d, c->stream));
   if (!brute) DKM_CK(launch_search(A, 0, c->d, c->stream));
   DKM_CK(launch_assign(A, c->d, brute, c->stream));
   DKM_CK(launch_collect(A, -1, c->stream));
@@ -463,6 +469,7 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
   do {
     if ((st = zero_run_buffers(c, early != 0)) != DKM_OK) break;
     if ((e = launch_centroids(A, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream))) break;
+    if (A.stay && (e = launch_cbound(A, 0, c->d, c->stream))) break;
     for (int t = 0; t < iters; ++t) {
       const int par = t & 1;
       if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, cudaEventRecordExternal))) break;
@@ -472,6 +479,7 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
       if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, cudaEventRecordExternal))) break;
       const int insert = !brute && t + 1 < iters;
       if ((e = launch_centroids(A, 1, t, c->d, nullptr, insert, par ^ 1, nullptr, c->stream))) break;
+      if (A.stay && insert && (e = launch_cbound(A, par ^ 1, c->d, c->stream))) break;
       if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, cudaEventRecordExternal))) break;
     }
   } while (0);
@@ -619,6 +627,7 @@ dkm_status apply_tiling(dkm_ctx* c) {
 dkm_status apply_units(dkm_ctx* c) {
   destroy_graph(c);
   DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
+  DKM_CK(cudaMemsetAsync(c->tlab, 0xff, sizeof(int) * c->tiles_cap, c->stream));
   if (c->unit_g <= 1) {
     c->n_units = c->n_tiles;
     return DKM_OK;
@@ -791,6 +800,8 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->ucloud = (int*)(base + P.ucloud);
   c->ufirst = (int*)(base + P.ufirst);
   c->tunit = (int*)(base + P.tunit);
+  c->cb2 = (float*)(base + P.cb2);
+  c->tlab = (int*)(base + P.tlab);
   c->wcnt = (int*)(base + P.wcnt);
   c->wbase = (int*)(base + P.wbase);
   c->level_hist = (unsigned long long*)(base + P.level_hist);
@@ -933,6 +944,8 @@ dkm_status tuning_check(const dkm_ctx* c, const dkm_tuning& t) {
     return fail(DKM_EINVAL, "sort_max must be in [0, 32] (got %d)", t.sort_max);
   if (t.tile_group < 1 || t.tile_group > 32)
     return fail(DKM_EINVAL, "tile_group must be in [1, 32] (got %d)", t.tile_group);
+  if (t.stay_test != 0 && t.stay_test != 1)
+    return fail(DKM_EINVAL, "stay_test must be 0 or 1 (got %d)", t.stay_test);
   return DKM_OK;
 }
 
@@ -958,6 +971,10 @@ dkm_status apply_tuning(dkm_ctx* c, const dkm_tuning& t) {
     c->sort_max = t.sort_max;
     changed = true;
   }
+  if (t.stay_test != c->stay) {
+    c->stay = t.stay_test;
+    changed = true;
+  }
   if (t.tile_group != c->unit_g) {
     c->unit_g = t.tile_group;
     DKM_TRY(apply_units(c));
@@ -978,6 +995,7 @@ dkm_tuning current_tuning(const dkm_ctx* c) {
   t.row_filter_min = c->row_filter_min;
   t.sort_max = c->sort_max;
   t.tile_group = c->unit_g;
+  t.stay_test = c->stay;
   return t;
 }
 
@@ -1090,6 +1108,11 @@ dkm_status autotune_impl(dkm_ctx* c, const float* init, int passes, int use_cach
     if (v == best.tile_group) continue;
     dkm_tuning t = best;
     t.tile_group = v;
+    DKM_TRY(trial(t));
+  }
+  if (best.tile_group == 1) {
+    dkm_tuning t = best;
+    t.stay_test = 1 - best.stay_test;
     DKM_TRY(trial(t));
   }
   DKM_TRY(apply_tuning(c, best));
@@ -1361,6 +1384,7 @@ dkm_status dkm_last_stats(dkm_ctx* c, dkm_stats* out) {
   out->tiles = (int64_t)c->n_tiles;
   out->tile_level = c->tile_level;
   out->fallback_tiles = (int64_t)h.last_fallback;
+  out->stayed_tiles = (int64_t)h.last_stays;
   out->grid_overflow = (int64_t)h.grid_ovf;
   out->passes = h.passes;
   return DKM_OK;

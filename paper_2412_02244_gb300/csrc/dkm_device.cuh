@@ -40,7 +40,8 @@ struct Slot {
   unsigned long long evals;     // point x candidate distance evaluations
   unsigned long long cands;     // sum of tile candidate-list lengths
   unsigned long long fallback;  // tiles whose candidate list overflowed
-  unsigned long long pad[5];
+  unsigned long long stays;     // tiles that passed the stay test (no search)
+  unsigned long long pad[4];
 };
 
 // Device-resident run state (whole context).
@@ -53,7 +54,7 @@ struct DevState {
   int err;               // internal error bits (kErr*)
   int label_err;         // dkm_update: a label outside [0, k_b)
   int pad0;
-  unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles;
+  unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles, last_stays;
   unsigned long long grid_ovf;   // centroids put in an overflow list, last rebuild
   double last_sse;               // total SSE of the last pass (against its input centroids)
   double final_sse;              // total SSE of the final labels against the final centroids
@@ -152,7 +153,20 @@ struct IterArgs {
   int early_stop;
   int row_filter_min;        // tile lists longer than this are filtered again per row
   int sort_max;              // lists up to this length (<= 32) are sorted, early exit
+  // Stay test (the bound layer): cb2[j] = squared distance from centroid j
+  // to the nearest other centroid of its cloud; tlab[t] = the single label
+  // of tile t in its last pass (-1: mixed or unknown).
+  int stay;
+  float* cb2;
+  int* tlab;
 };
+
+// A tile whose box lies within cb[a]/2 of centroid a (maxd^2 <= kStay *
+// cb[a]^2) has a as the unique nearest centroid of every point in it: for
+// any other c_j, |p - c_j| >= cb[a] - |p - c_a| > |p - c_a|.  kStay =
+// 1/4 (1 - 2^-9) keeps the relative gap of the squared distances above
+// 2^-9, far above FP32 rounding.
+constexpr float kStay = 0.25f * (1.0f - 1.0f / 512.0f);
 
 // ---------------------------------------------------------------------------
 // exact helpers

@@ -45,6 +45,7 @@ cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
 cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int32_t* labels_out,
                             int do_sse, cudaStream_t s);
 cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s);
+cudaError_t launch_cbound(const IterArgs& A, int par, int d, cudaStream_t s);
 cudaError_t launch_unit_boxes(const float4* tbox, const int* tcloud, const int* ufirst,
                               int n_units, float4* ubox, int* ucloud, int* tunit,
                               cudaStream_t s);
@@ -89,6 +90,7 @@ struct dkm_ctx {
   std::vector<float> h_blo, h_bhi;                // per-cloud point boxes (3 floats each)
   int row_filter_min = 48;     // per-row candidate filtering threshold
   int sort_max = 0;            // sorted early-exit evaluation for lists up to this length
+  int stay = 0;                // the bound layer's stay test (tile_group 1 only)
   bool ready = false;          // the point index is valid
   bool acc_valid = false;      // acc holds the sums of the last dkm_assign
 
@@ -106,6 +108,8 @@ struct dkm_ctx {
   int* n_tiles_dev = nullptr;
   int* tcloud = nullptr;
   int* kcloud = nullptr;
+  float* cb2 = nullptr;        // per centroid: squared gap to its nearest other centroid
+  int* tlab = nullptr;         // per tile: single label of its last pass, or -1
   float4* ubox = nullptr;      // per unit box (unit_g > 1)
   int *ucloud = nullptr, *ufirst = nullptr, *tunit = nullptr;
   int *wcnt = nullptr, *wbase = nullptr;

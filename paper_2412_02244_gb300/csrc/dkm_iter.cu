@@ -46,10 +46,10 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long
 // Sums over clouds run in a fixed order, so the totals are deterministic.
 __device__ void collect_pass(const IterArgs& A, int t) {
   __shared__ double s_sse[kBlockThreads / 32];
-  __shared__ unsigned long long s_part[5][kBlockThreads / 32];
+  __shared__ unsigned long long s_part[6][kBlockThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double sse = 0.0;
-  unsigned long long v[5] = {0, 0, 0, 0, 0};   // changed, evals, cands, fallback, clouds run
+  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};   // changed, evals, cands, fallback, clouds run, stays
   for (int b = threadIdx.x; b < A.B; b += blockDim.x) {
     CloudRun& r = A.crun[b];
     if (t >= 0 && r.passes != t + 1) continue;   // the cloud stopped earlier
@@ -80,24 +80,24 @@ __device__ void collect_pass(const IterArgs& A, int t) {
   if (t != -2) {
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
       Slot& s = A.slots[i];
-      v[1] += s.evals; v[2] += s.cands; v[3] += s.fallback;
-      s.evals = 0; s.cands = 0; s.fallback = 0;
+      v[1] += s.evals; v[2] += s.cands; v[3] += s.fallback; v[5] += s.stays;
+      s.evals = 0; s.cands = 0; s.fallback = 0; s.stays = 0;
     }
   }
   for (int o = 16; o > 0; o >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, o);
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < 6; ++q) {
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     if (lane == 0) s_part[q][w] = v[q];
   }
   if (lane == 0) s_sse[w] = sse;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long tot[5] = {0, 0, 0, 0, 0};
+    unsigned long long tot[6] = {0, 0, 0, 0, 0, 0};
     double tsse = 0.0;
     for (int ww = 0; ww < (int)(blockDim.x / 32); ++ww) {
       tsse += s_sse[ww];
-      for (int q = 0; q < 5; ++q) tot[q] += s_part[q][ww];
+      for (int q = 0; q < 6; ++q) tot[q] += s_part[q][ww];
     }
     if (t == -2) {   // final SSE of a run: leave the last-pass counters alone
       A.st->final_sse = tsse;
@@ -107,6 +107,7 @@ __device__ void collect_pass(const IterArgs& A, int t) {
       A.st->last_evals = tot[1];
       A.st->last_cands = tot[2];
       A.st->last_fallback = tot[3];
+      A.st->last_stays = tot[5];
       A.st->last_tiles = (unsigned long long)A.n_tiles;
       if (t >= 0 && tot[4] > 0) {
         A.sse_hist[t] = tsse;
@@ -258,6 +259,22 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   const Grid G = cl.grid;
   const int c0 = cl.c0, c1 = cl.c0 + cl.k;
   const float4 lo = A.ubox[2 * t], hi = A.ubox[2 * t + 1];
+  if (A.stay) {   // the bound layer: a tile inside half the gap of its last label stays
+    const int a = A.tlab[t];
+    if (a >= 0) {
+      const float4 c = A.cw[a];
+      if (maxd2(lo, hi, c.x, c.y, c.z, d) <= kStay * A.cb2[a]) {
+        if (lane == 0) {
+          out[0] = c;
+          A.tcnt[t] = 1;
+          Slot& s = A.slots[t & (kSlots - 1)];
+          red_add_u64(&s.cands, 1ull);
+          red_add_u64(&s.stays, 1ull);
+        }
+        return;
+      }
+    }
+  }
   const int* __restrict__ gcnt = A.gcnt[par] + cl.cell0;
   const float4* __restrict__ gbkt = A.gbkt[par] + cl.cell0 * kBucketCap;
   const int n_ovf = A.ovf_cnt[par][b];
@@ -607,9 +624,10 @@ __device__ __forceinline__ int filter_list(const float4* __restrict__ src, int m
 // one group; otherwise every point loads its own centroid and the labels
 // are taken one at a time (the smallest pending label of the warp).  The
 // sums depend only on the tile and the labels, so every caller gets the
-// same sums bit for bit.
+// same sums bit for bit.  Returns the tile's label when all its points
+// share one, else -1.
 template <int D>
-__device__ __forceinline__ void accumulate_tile(const IterArgs& A, const float2 (&px)[kRowsPerWarp],
+__device__ __forceinline__ int accumulate_tile(const IterArgs& A, const float2 (&px)[kRowsPerWarp],
                                                 const float2 (&py)[kRowsPerWarp],
                                                 const float2 (&pz)[kRowsPerWarp],
                                                 const int2 (&lab)[kRowsPerWarp],
@@ -630,7 +648,7 @@ __device__ __forceinline__ void accumulate_tile(const IterArgs& A, const float2 
 #pragma unroll
   for (int h = 0; h < H; ++h) lmin = pend[h] ? min(lmin, lb[h]) : lmin;
   int L = __reduce_min_sync(0xffffffffu, lmin);
-  if (L == INT_MAX) return;   // no valid point
+  if (L == INT_MAX) return -1;   // no valid point
   bool same = true;
 #pragma unroll
   for (int h = 0; h < H; ++h) same = same && (!pend[h] || lb[h] == L);
@@ -681,9 +699,9 @@ __device__ __forceinline__ void accumulate_tile(const IterArgs& A, const float2 
     if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     if (lane == 0) add_group(A, D, L, sx, sy, sz, cnt, s_t, s_glob);
-    if (single) break;
+    if (single) return L;
     L = __reduce_min_sync(0xffffffffu, lmin);
-    if (L == INT_MAX) break;
+    if (L == INT_MAX) return -1;
   }
 }
 
@@ -892,9 +910,10 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
     }
   }
   sse = tile_sse(best, va, vb, s_sse);
-  accumulate_tile<D>(A, P.x, P.y, P.z, bid, va, vb, s_glob);
+  const int single = accumulate_tile<D>(A, P.x, P.y, P.z, bid, va, vb, s_glob);
   changed = __reduce_add_sync(0xffffffffu, changed);
   if (lane == 0) {
+    if (A.stay) A.tlab[t] = single;
     CloudAcc& ca = A.cacc[b];
     red_add_u64(&ca.sse[t & (kCloudSlots - 1)], (unsigned long long)sse);
     if (changed) red_add_u64(&ca.changed[t & (kCloudSlots - 1)], (unsigned long long)changed);
@@ -1082,6 +1101,79 @@ cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int3
 
 cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s) {
   k_export<<<ceil_div(k, 256), 256, 0, s>>>(cw, k, d, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k_cbound: cb2[j] = squared distance from centroid j to the nearest other
+// centroid of its cloud (the paper's per-iteration kNN(2) over the
+// centroids), from the grid of parity `par` just built.  Rings of cells
+// around c_j's cell are scanned until the best distance found is within
+// the ring's lower bound: a centroid whose cell lies beyond ring r is at
+// least r cell edges away.  Both the bound and the final value err low
+// (slack 2^-8), so cb2 never exceeds the true squared gap by more than
+// rounding and the stay test stays conservative.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) k_cbound(IterArgs A, int par, int d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= A.k) return;
+  const int b = A.kcloud[j];
+  if (A.crun[b].done) return;
+  const Cloud& cl = A.clouds[b];
+  const float4 c = A.cw[j];
+  float best = INFINITY;
+  auto take = [&](const float4& e) {
+    if (__float_as_int(e.w) == j) return;
+    const float dx = __fadd_rn(e.x, -c.x), dy = __fadd_rn(e.y, -c.y), dz = __fadd_rn(e.z, -c.z);
+    best = fminf(best, __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+  };
+  const int n_ovf = A.ovf_cnt[par][b];
+  for (int q = 0; q < n_ovf; ++q) take(A.ovf[par][cl.c0 + q]);
+  const Grid& G = cl.grid;
+  const int* __restrict__ gcnt = A.gcnt[par] + cl.cell0;
+  const float4* __restrict__ gbkt = A.gbkt[par] + cl.cell0 * kBucketCap;
+  const int cc[3] = {cell_coord(c.x, G.g0[0], G.inv_s, G.dims[0]),
+                     cell_coord(c.y, G.g0[1], G.inv_s, G.dims[1]),
+                     d == 3 ? cell_coord(c.z, G.g0[2], G.inv_s, G.dims[2]) : 0};
+  const float edge = 1.0f / G.inv_s;
+  // cell coordinates carry FP32 rounding of up to ~dims * 2^-24 cells
+  const int dmax = max(max(G.dims[0], G.dims[1]), G.dims[2]);
+  const float margin = 1.0f / 64.0f + (float)dmax * (1.0f / 1048576.0f);
+  const long long flat_cells = (long long)(cl.k / 4) + 32;
+  for (int r = 0;; ++r) {
+    int lo[3], hi[3];
+    long long ncell = 1;
+    bool whole = true;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = max(cc[a] - r, 0);
+      hi[a] = min(cc[a] + r, G.dims[a] - 1);
+      whole = whole && lo[a] == 0 && hi[a] == G.dims[a] - 1;
+      ncell *= (long long)(hi[a] - lo[a] + 1);
+    }
+    if (ncell > flat_cells) {   // large rings: every centroid of the cloud once
+      best = INFINITY;
+      for (int q = cl.c0; q < cl.c0 + cl.k; ++q) take(A.cw[q]);
+      break;
+    }
+    // the shell of ring r (cells at Chebyshev distance exactly r)
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          const int cheb = max(max(abs(x - cc[0]), abs(y - cc[1])), abs(z - cc[2]));
+          if (cheb != r) continue;
+          const long long cell = ((long long)z * G.dims[1] + y) * G.dims[0] + x;
+          const int cnt = min(gcnt[cell], kBucketCap);
+          for (int i = 0; i < cnt; ++i) take(gbkt[cell * kBucketCap + i]);
+        }
+    if (whole) break;
+    const float lb = fmaxf((float)r - margin, 0.f) * edge;
+    if (best <= lb * lb * (1.0f - 1.0f / 256.0f)) break;
+  }
+  A.cb2[j] = best * (1.0f - 1.0f / 256.0f);
+}
+
+cudaError_t launch_cbound(const IterArgs& A, int par, int d, cudaStream_t s) {
+  k_cbound<<<ceil_div(A.k, kBlockThreads), kBlockThreads, 0, s>>>(A, par, d);
   return cudaGetLastError();
 }
 

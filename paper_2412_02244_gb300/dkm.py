@@ -53,14 +53,15 @@ class dkm_timings(ctypes.Structure):
 
 class dkm_stats(ctypes.Structure):
     _fields_ = [("evals_per_point", ctypes.c_double), ("candidates_per_tile", ctypes.c_double),
-                ("fallback_tiles", ctypes.c_int64), ("grid_overflow", ctypes.c_int64),
+                ("fallback_tiles", ctypes.c_int64), ("stayed_tiles", ctypes.c_int64),
+                ("grid_overflow", ctypes.c_int64),
                 ("tiles", ctypes.c_int64), ("tile_level", ctypes.c_int), ("passes", ctypes.c_int)]
 
 
 class dkm_tuning(ctypes.Structure):
     _fields_ = [("cells_per_centroid", ctypes.c_float), ("tile_cut_div", ctypes.c_int),
                 ("row_filter_min", ctypes.c_int), ("sort_max", ctypes.c_int),
-                ("tile_group", ctypes.c_int),
+                ("tile_group", ctypes.c_int), ("stay_test", ctypes.c_int),
                 ("ms_per_pass", ctypes.c_float),
                 ("ms_per_pass_before", ctypes.c_float), ("trials", ctypes.c_int),
                 ("from_cache", ctypes.c_int)]

@@ -204,7 +204,8 @@ def test_batched_uneven_workload_full_size(dkm, oracle):
                                      dict(row_filter_min=16), dict(row_filter_min=256),
                                      dict(sort_max=32), dict(sort_max=16),
                                      dict(tile_group=4), dict(tile_group=32),
-                                     dict(tile_group=8, sort_max=32)])
+                                     dict(tile_group=8, sort_max=32), dict(stay_test=1),
+                                     dict(stay_test=1, sort_max=32)])
 def test_tuning_settings_keep_labels_exact(dkm, setting):
     """Every index setting labels exactly like brute force.  The SSE is a sum
     of per-tile fixed-point partials (each tile at its own power-of-two
@@ -236,6 +237,7 @@ def test_autotune_choice_cache_and_exactness(dkm):
     assert t.cells_per_centroid in (0.5, 1.0, 2.0, 4.0)
     assert t.tile_cut_div in (2, 4, 8, 16, 32) and t.row_filter_min in (16, 32, 48, 96, 256)
     assert t.sort_max in (0, 16, 32) and t.tile_group in (1, 2, 4, 8, 16)
+    assert t.stay_test in (0, 1)
     cur = dkm.dkm_get_tuning(ctx)
     assert (cur.cells_per_centroid, cur.tile_cut_div, cur.row_filter_min) == \
         (t.cells_per_centroid, t.tile_cut_div, t.row_filter_min)
@@ -253,9 +255,35 @@ def test_tuning_rejects_bad_values(dkm):
     ctx = _ctx(dkm, P, off, ks)
     for kw in (dict(cells_per_centroid=0.0), dict(cells_per_centroid=100.0),
                dict(tile_cut_div=1), dict(row_filter_min=-1), dict(sort_max=33),
-               dict(tile_group=0), dict(tile_group=33)):
+               dict(tile_group=0), dict(tile_group=33), dict(stay_test=2)):
         with pytest.raises(dkm.DkmError) as e:
             dkm.dkm_set_tuning(ctx, **kw)
         assert e.value.status == dkm.DKM_EINVAL
     with pytest.raises(dkm.DkmError):
         dkm.dkm_autotune(ctx, dev(init), passes=0)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_stay_test_gives_the_same_run_bit_for_bit(dkm, batched):
+    """The bound layer only skips searches whose outcome it has proved, so a
+    run with it equals the run without it in every bit, and near
+    convergence some tiles do stay."""
+    if batched:
+        P, off, ks, coff, init = _small(3, seed=57, n_clouds=6)
+    else:
+        w = synth.lidar3d(seed=58, n=60_011, k=60, n_objects=20)
+        P, init = np.ascontiguousarray(w.points), w.init
+        off, ks = np.array([0, w.n], np.int64), np.array([w.k], np.int32)
+    out = []
+    for stay in (0, 1):
+        ctx = _ctx(dkm, P, off, ks, early_stop=0)
+        dkm.dkm_set_tuning(ctx, stay_test=stay)
+        out.append(_run(dkm, ctx, init, 12))
+        st = dkm.dkm_last_stats(ctx)
+        if stay:
+            assert st.stayed_tiles > 0
+        else:
+            assert st.stayed_tiles == 0
+    (C0, l0, i0, s0), (C1, l1, i1, s1) = out
+    assert np.array_equal(C0, C1) and np.array_equal(l0, l1)
+    assert np.array_equal(i0, i1) and np.array_equal(s0, s1)
