@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "0002192177e468ce", "bytes_per_launch": 127_327_744 + 21_182_720,
+NCU_TRAFFIC = {"sha": "c2e60855d00e45d3", "bytes_per_launch": 134_206_464 + 22_245_120,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
