@@ -167,7 +167,7 @@ struct Layout {
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
   size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles,
-      tcloud, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
 };
@@ -199,6 +199,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.tiles = L.take<int2>(tm);
   P.n_tiles = L.take<int>(1);
   P.tcloud = L.take<int>(tm);
+  P.tfirst = L.take<int>(B);
   P.kcloud = L.take<int>(k);
   P.ubox = L.take<float4>(2 * tm);
   P.ucloud = L.take<int>(tm);
@@ -254,6 +255,7 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.n_tiles = c->n_tiles;
   A.tiles = c->tiles;
   A.tcloud = c->tcloud;
+  A.tfirst = c->tfirst;
   A.kcloud = c->kcloud;
   A.unit_g = c->unit_g;
   A.n_units = c->n_units;
@@ -309,24 +311,52 @@ dkm_status check_ctx(const dkm_ctx* c) {
   return DKM_OK;
 }
 
-dkm_status read_state(dkm_ctx* c, DevState* h) {
-  DKM_CK(cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-  DKM_CK(cudaStreamSynchronize(c->stream));
-  return DKM_OK;
+// Pinned staging block of a context: DevState, then B CloudRun, then B
+// Cloud (copies from and to it are truly asynchronous).
+size_t pin_bytes(int B) {
+  return align_up(sizeof(DevState), 256) + align_up(sizeof(CloudRun) * B, 256) +
+         sizeof(Cloud) * B;
+}
+DevState* pin_state(dkm_ctx* c) { return (DevState*)c->hpin; }
+CloudRun* pin_crun(dkm_ctx* c) {
+  return (CloudRun*)((char*)c->hpin + align_up(sizeof(DevState), 256));
+}
+Cloud* pin_clouds(dkm_ctx* c) {
+  return (Cloud*)((char*)pin_crun(c) + align_up(sizeof(CloudRun) * c->B, 256));
 }
 
-dkm_status read_clouds(dkm_ctx* c, std::vector<CloudRun>* h) {
-  h->resize(c->B);
-  DKM_CK(cudaMemcpyAsync(h->data(), c->crun, sizeof(CloudRun) * c->B, cudaMemcpyDeviceToHost,
+dkm_status read_state(dkm_ctx* c, DevState* h) {
+  DKM_CK(cudaMemcpyAsync(pin_state(c), c->st, sizeof(DevState), cudaMemcpyDeviceToHost,
                          c->stream));
   DKM_CK(cudaStreamSynchronize(c->stream));
+  *h = *pin_state(c);
   return DKM_OK;
 }
 
-dkm_status upload_clouds(dkm_ctx* c) {
-  DKM_CK(cudaMemcpyAsync(c->clouds, c->h_clouds.data(), sizeof(Cloud) * c->B,
-                         cudaMemcpyHostToDevice, c->stream));
+// run state and every cloud's state with one synchronisation
+dkm_status read_state_clouds(dkm_ctx* c, DevState* h, std::vector<CloudRun>* hr) {
+  DKM_CK(cudaMemcpyAsync(pin_state(c), c->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                         c->stream));
+  DKM_CK(cudaMemcpyAsync(pin_crun(c), c->crun, sizeof(CloudRun) * c->B, cudaMemcpyDeviceToHost,
+                         c->stream));
   DKM_CK(cudaStreamSynchronize(c->stream));
+  if (h) *h = *pin_state(c);
+  hr->assign(pin_crun(c), pin_crun(c) + c->B);
+  return DKM_OK;
+}
+
+dkm_status read_clouds(dkm_ctx* c, std::vector<CloudRun>* hr) {
+  return read_state_clouds(c, nullptr, hr);
+}
+
+// Stream-ordered upload of the host cloud table.  The staging block may be
+// rewritten before an earlier copy has run; that copy then carries newer
+// values, and the last copy, issued after the last host change, lands
+// before any later kernel.
+dkm_status upload_clouds(dkm_ctx* c) {
+  memcpy(pin_clouds(c), c->h_clouds.data(), sizeof(Cloud) * c->B);
+  DKM_CK(cudaMemcpyAsync(c->clouds, pin_clouds(c), sizeof(Cloud) * c->B, cudaMemcpyHostToDevice,
+                         c->stream));
   return DKM_OK;
 }
 
@@ -612,11 +642,7 @@ dkm_status apply_tiling(dkm_ctx* c) {
   // candidate lists of the old tiles must not seed the new ones
   DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
   DKM_CK(launch_tile_boxes(c->xs, c->ys, c->zs, c->d, c->tiles, nt, c->skeys, c->mb, c->B,
-                           c->tbox, c->tcloud, c->clouds, c->stream));
-  // the kernel filled each cloud's first tile: refresh the host copy
-  DKM_CK(cudaMemcpyAsync(c->h_clouds.data(), c->clouds, sizeof(Cloud) * c->B,
-                         cudaMemcpyDeviceToHost, c->stream));
-  DKM_CK(cudaStreamSynchronize(c->stream));
+                           c->tbox, c->tcloud, c->tfirst, c->stream));
   return apply_units(c);
 }
 
@@ -632,11 +658,15 @@ dkm_status apply_units(dkm_ctx* c) {
     c->n_units = c->n_tiles;
     return DKM_OK;
   }
+  std::vector<int> tf(c->B);
+  DKM_CK(cudaMemcpyAsync(tf.data(), c->tfirst, sizeof(int) * c->B, cudaMemcpyDeviceToHost,
+                         c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
   std::vector<int> uf;
   uf.reserve((size_t)c->n_tiles / c->unit_g + c->B + 1);
   for (int b = 0; b < c->B; ++b) {
-    const int t_begin = c->h_clouds[b].t0;
-    const int t_end = b + 1 < c->B ? c->h_clouds[b + 1].t0 : c->n_tiles;
+    const int t_begin = tf[b];
+    const int t_end = b + 1 < c->B ? tf[b + 1] : c->n_tiles;
     for (int t = t_begin; t < t_end; t += c->unit_g) uf.push_back(t);
   }
   uf.push_back(c->n_tiles);
@@ -675,10 +705,9 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   if (c->opts.profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
   DKM_CK(launch_bbox(src, c->d, c->doff, c->B, c->max_n_b, c->crun, c->st, 0, c->d, c->stream));
   DevState h;
-  DKM_TRY(read_state(c, &h));
-  if (h.bad) return fail(DKM_EINVAL, "points contain a non-finite or |x| > 1e18 coordinate");
   std::vector<CloudRun> hr;
-  DKM_TRY(read_clouds(c, &hr));
+  DKM_TRY(read_state_clouds(c, &h, &hr));
+  if (h.bad) return fail(DKM_EINVAL, "points contain a non-finite or |x| > 1e18 coordinate");
   cloud_boxes(c, hr, &c->h_blo, &c->h_bhi);
   const std::vector<float>& blo = c->h_blo;
   const std::vector<float>& bhi = c->h_bhi;
@@ -695,8 +724,13 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   DKM_CK(launch_morton(src, c->n, c->d, c->doff, c->B, c->clouds, c->mb, c->keys[0], c->vals[0],
                        c->stream));
   int fin = 0;
-  DKM_CK(launch_radix_sort(c->keys, c->vals, c->n, c->key_bits, c->rs_counts, c->rs_totals, &fin,
-                           c->stream));
+  // The top 24 key bits are sorted: the lower ones only order points inside
+  // the finest Morton cells, far below the cube level tiles are cut at, and
+  // every order is a valid index (tiles are cut wherever the compared key
+  // bits change, and boxes are taken from the points themselves).
+  const int bits_lo = c->key_bits > 24 ? c->key_bits - 24 : 0;
+  DKM_CK(launch_radix_sort(c->keys, c->vals, c->n, bits_lo, c->key_bits, c->rs_counts,
+                           c->rs_totals, &fin, c->stream));
   c->perm = c->vals[fin];
   c->skeys = c->keys[fin];
   DKM_CK(launch_gather(src, c->n, c->d, c->perm, c->xs, c->ys, c->zs, c->n_pad, c->stream));
@@ -795,6 +829,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->tiles = (int2*)(base + P.tiles);
   c->n_tiles_dev = (int*)(base + P.n_tiles);
   c->tcloud = (int*)(base + P.tcloud);
+  c->tfirst = (int*)(base + P.tfirst);
   c->kcloud = (int*)(base + P.kcloud);
   c->ubox = (float4*)(base + P.ubox);
   c->ucloud = (int*)(base + P.ucloud);
@@ -843,6 +878,11 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
       cudaEventCreate(&c->ev_c) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(DKM_ECUDA, "context initialisation failed"));
+  }
+  if (cudaMallocHost(&c->hpin, pin_bytes(c->B)) != cudaSuccess) {
+    cudaGetLastError();
+    c->hpin = nullptr;
+    return bail(fail(DKM_ENOMEM, "pinned host staging allocation failed"));
   }
   dkm_status s = setup_impl(c, points);
   if (s != DKM_OK) return bail(s);
@@ -1402,6 +1442,7 @@ void dkm_destroy(dkm_ctx* c) {
   if (c->lstage) cudaFree(c->lstage);
   if (c->sse_hist) cudaFree(c->sse_hist);
   if (c->chg_hist) cudaFree(c->chg_hist);
+  if (c->hpin) cudaFreeHost(c->hpin);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

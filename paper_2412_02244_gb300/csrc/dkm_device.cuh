@@ -90,7 +90,7 @@ struct Cloud {
   float mlo[3];          // Morton lattice: origin and 1 / step
   float minv;
   int shift;             // tiles are cut where (key >> shift) changes
-  int t0;                // its first tile
+  int pad;
 };
 
 // Per-cloud run state.
@@ -121,6 +121,7 @@ struct IterArgs {
   int n_tiles;               // tiles of the point index (launch size)
   const int2* tiles;         // per tile: [start, end) in sorted order
   const int* tcloud;         // per tile: its cloud
+  const int* tfirst;         // per cloud: its first tile
   // Search units: tile_group consecutive tiles of one cloud share one grid
   // search (unit_g = 1: every tile is its own unit, ubox = tbox).
   int unit_g;

@@ -20,8 +20,9 @@ cudaError_t launch_morton(const float* p, int64_t n, int d, const int64_t* seg, 
                           const Cloud* clouds, int mb, uint32_t* keys, uint32_t* vals,
                           cudaStream_t s);
 int64_t radix_sort_nb(int64_t n);
-cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits,
-                              uint32_t* counts, uint32_t* totals, int* final_buf, cudaStream_t s);
+cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits_lo,
+                              int bits_hi, uint32_t* counts, uint32_t* totals, int* final_buf,
+                              cudaStream_t s);
 cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,
                           float* ys, float* zs, int64_t n_pad, cudaStream_t s);
 cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,
@@ -31,7 +32,7 @@ cudaError_t launch_tiles(const uint32_t* keys, int64_t n, const Cloud* clouds, i
                          cudaStream_t s);
 cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
                               const int2* tiles, int n_tiles, const uint32_t* keys, int mb, int B,
-                              float4* tbox, int* tcloud, Cloud* clouds, cudaStream_t s);
+                              float4* tbox, int* tcloud, int* tfirst, cudaStream_t s);
 
 // dkm_iter.cu
 cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s);
@@ -107,6 +108,7 @@ struct dkm_ctx {
   int2* tiles = nullptr;
   int* n_tiles_dev = nullptr;
   int* tcloud = nullptr;
+  int* tfirst = nullptr;       // per cloud: its first tile
   int* kcloud = nullptr;
   float* cb2 = nullptr;        // per centroid: squared gap to its nearest other centroid
   int* tlab = nullptr;         // per tile: single label of its last pass, or -1
@@ -132,6 +134,9 @@ struct dkm_ctx {
   float* cstage = nullptr;     // k x d centroid staging
   float* cstage2 = nullptr;    // k x d centroid output staging
   int32_t* kstage = nullptr;   // k counts staging
+
+  // pinned host staging: DevState, then B CloudRun, then B Cloud
+  void* hpin = nullptr;
 
   // lazily allocated
   double* sse_hist = nullptr;

@@ -756,7 +756,7 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
   if (MULTI && A.crun[b].done) return;
   const Cloud& cl = MULTI ? A.clouds[b] : A.cl0;
   const int c0 = cl.c0, c1 = cl.c0 + cl.k;
-  if (t == cl.t0 && lane == 0) A.crun[b].passes += 1;   // one writer per cloud
+  if (t == (MULTI ? A.tfirst[b] : 0) && lane == 0) A.crun[b].passes += 1;   // one writer per cloud
   const int2 se = A.tiles[t];
   const int64_t base = (int64_t)(se.x / kTilePts) * kTilePts;
 

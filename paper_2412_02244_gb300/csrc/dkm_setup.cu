@@ -232,13 +232,19 @@ __global__ void __launch_bounds__(256) k_rs_scan(uint32_t* __restrict__ counts, 
   if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
+// The CTA's keys are first placed in shared memory grouped by digit (stable:
+// warp, then item, then lane order), then written out digit run by digit
+// run, so consecutive threads store to consecutive addresses.
 __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ counts,
     const uint32_t* __restrict__ totals, int nb) {
   __shared__ uint32_t whist[8][256];
   __shared__ uint32_t goff[256];
+  __shared__ uint32_t lbase[256];
   __shared__ uint32_t s_warp[16];
+  __shared__ uint32_t skey[kRsTile];
+  __shared__ uint32_t sval[kRsTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < 8 * 256; t += kRsThreads) (&whist[0][0])[t] = 0;
   uint32_t tot = totals[threadIdx.x];
@@ -246,7 +252,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
   goff[threadIdx.x] = digit_base + counts[(int64_t)threadIdx.x * nb + blockIdx.x];
   __syncthreads();
 
-  const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)w * (32 * kRsItems);
+  const int64_t cta0 = (int64_t)blockIdx.x * kRsTile;
+  const int64_t base = cta0 + (int64_t)w * (32 * kRsItems);
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t key[kRsItems], val[kRsItems], rank[kRsItems];
 #pragma unroll
@@ -270,24 +277,35 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
     rank[j] = b + (uint32_t)__popc(peers & lt);
   }
   __syncthreads();
+  uint32_t run = 0;
   {   // per digit: exclusive prefix over warps (warp order = input order)
-    uint32_t run = 0;
     for (int ww = 0; ww < 8; ++ww) {
       uint32_t c = whist[ww][threadIdx.x];
       whist[ww][threadIdx.x] = run;
       run += c;
     }
   }
+  // start of each digit's run inside this CTA's block of keys
+  lbase[threadIdx.x] = block_exclusive_scan256(run, s_warp, nullptr);
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kRsItems; ++j) {
     int64_t i = base + j * 32 + lane;
     if (i < n) {
       uint32_t dig = (key[j] >> shift) & 0xffu;
-      uint32_t pos = goff[dig] + whist[w][dig] + rank[j];
-      kout[pos] = key[j];
-      vout[pos] = val[j];
+      uint32_t loc = lbase[dig] + whist[w][dig] + rank[j];
+      skey[loc] = key[j];
+      sval[loc] = val[j];
     }
+  }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)kRsTile, n - cta0);
+  for (int i = threadIdx.x; i < cnt; i += kRsThreads) {
+    const uint32_t k = skey[i];
+    const uint32_t dig = (k >> shift) & 0xffu;
+    const uint32_t pos = goff[dig] + ((uint32_t)i - lbase[dig]);
+    kout[pos] = k;
+    vout[pos] = sval[i];
   }
 }
 
@@ -440,7 +458,7 @@ __global__ void __launch_bounds__(256) k_tile_boxes(const float* __restrict__ xs
                                                     const uint32_t* __restrict__ keys, int mb,
                                                     int B, float4* __restrict__ tbox,
                                                     int* __restrict__ tcloud,
-                                                    Cloud* __restrict__ clouds) {
+                                                    int* __restrict__ tfirst) {
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (t >= n_tiles) return;
@@ -463,7 +481,7 @@ __global__ void __launch_bounds__(256) k_tile_boxes(const float* __restrict__ xs
     tbox[2 * t + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
     const int b = cloud_of_key(keys[se.x], d, mb, B);
     tcloud[t] = b;
-    if (se.x == 0 || cloud_of_key(keys[se.x - 1], d, mb, B) != b) clouds[b].t0 = t;
+    if (se.x == 0 || cloud_of_key(keys[se.x - 1], d, mb, B) != b) tfirst[b] = t;
   }
 }
 
@@ -498,12 +516,12 @@ cudaError_t launch_morton(const float* p, int64_t n, int d, const int64_t* seg, 
 
 int64_t radix_sort_nb(int64_t n) { return (n + kRsTile - 1) / kRsTile; }
 
-cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits,
-                              uint32_t* counts, uint32_t* totals, int* final_buf,
+cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits_lo,
+                              int bits_hi, uint32_t* counts, uint32_t* totals, int* final_buf,
                               cudaStream_t s) {
   int nb = (int)radix_sort_nb(n);
   int cur = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = bits_lo; shift < bits_hi; shift += 8) {
     k_rs_upsweep<<<nb, kRsThreads, 0, s>>>(keys[cur], n, shift, counts, nb);
     k_rs_scan<<<256, 256, 0, s>>>(counts, nb, totals);
     k_rs_downsweep<<<nb, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1],
@@ -548,9 +566,9 @@ cudaError_t launch_tiles(const uint32_t* keys, int64_t n, const Cloud* clouds, i
 
 cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
                               const int2* tiles, int n_tiles, const uint32_t* keys, int mb, int B,
-                              float4* tbox, int* tcloud, Cloud* clouds, cudaStream_t s) {
+                              float4* tbox, int* tcloud, int* tfirst, cudaStream_t s) {
   k_tile_boxes<<<(n_tiles + 7) / 8, 256, 0, s>>>(xs, ys, zs, d, tiles, n_tiles, keys, mb, B, tbox,
-                                                 tcloud, clouds);
+                                                 tcloud, tfirst);
   return cudaGetLastError();
 }
 
