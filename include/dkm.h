@@ -100,11 +100,12 @@ typedef struct {
 typedef struct {
     float setup_ms;         /* last dkm_setup: bbox, Morton sort, tile boxes */
     float iterations_ms;    /* last dkm_run: all passes (graph launch) */
-    float search_ms;        /* mean per pass: per-block candidate search */
-    float assign_ms;        /* mean per pass: assignment + accumulation kernel */
-    float update_ms;        /* mean per pass: centroid update + grid rebuild */
+    float search_ms;        /* mean per profiled pass: candidate search */
+    float assign_ms;        /* mean per profiled pass: assignment + accumulation kernel */
+    float update_ms;        /* mean per profiled pass: centroid update + grid rebuild */
     float finalize_ms;      /* last dkm_run: label un-permute + final SSE */
-    int passes;             /* passes the timings cover */
+    int passes;             /* profiled passes the means cover: every fifth pass
+                               (every pass of a run of up to five) */
 } dkm_timings;
 
 typedef struct {
@@ -316,9 +317,11 @@ DKM_API dkm_status dkm_query_memory(const dkm_ctx* ctx, size_t* device_bytes, si
 /* Plan the context was built with. */
 DKM_API dkm_status dkm_get_plan(const dkm_ctx* ctx, dkm_plan_info* out);
 
-/* Timings of the last dkm_setup / dkm_run (needs opts.profile for the
- * per-kernel means; otherwise those are 0). */
-DKM_API dkm_status dkm_last_timings(const dkm_ctx* ctx, dkm_timings* out);
+/* Timings of the last dkm_setup / dkm_run (needs opts.profile; otherwise
+ * 0).  CUDA events are recorded around the kernels of every fifth pass, so
+ * profiling adds few graph nodes; the setup time is read out here (this
+ * call may wait for the last dkm_setup to finish). */
+DKM_API dkm_status dkm_last_timings(dkm_ctx* ctx, dkm_timings* out);
 
 /* Pruning counters of the last pass (reads device counters; synchronises
  * the context's stream). */

@@ -288,6 +288,8 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.chg_hist = c->chg_hist;
   A.track_changes = track_changes;
   A.early_stop = early_stop;
+  A.want_sse = 1;
+  A.want_stats = 1;
   A.row_filter_min = c->row_filter_min;
   A.sort_max = c->sort_max;
   A.stay = (c->stay && c->unit_g == 1 && c->opts.algo != DKM_ALGO_BRUTE) ? 1 : 0;
@@ -484,10 +486,25 @@ dkm_status check_state(const DevState& h) {
   return DKM_OK;
 }
 
+// The cached graph can be relaunched: same loop shape, and every kernel
+// argument it captured (tile and unit counts, grids, cloud 0's table,
+// settings) equal to the current ones.
+bool graph_current(const dkm_ctx* c, int iters, int early, int profile) {
+  if (!c->gexec || c->g_iters != iters || c->g_algo != c->opts.algo || c->g_early != early ||
+      c->g_profile != profile)
+    return false;
+  const IterArgs now = iter_args(c, early, early);
+  return memcmp(&now, &c->g_args, sizeof(IterArgs)) == 0;
+}
+
+// Passes whose kernels get CUDA events when profiling: every fifth pass (all
+// of a run of up to five), so the event nodes stay few in long runs.
+bool profiled_pass(int t, int iters) { return iters <= 5 || t % 5 == 4; }
+
 dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
   destroy_graph(c);
   const int brute = c->opts.algo == DKM_ALGO_BRUTE;
-  IterArgs A = iter_args(c, early, early);
+  const IterArgs A0 = iter_args(c, early, early);
   if (profile) {
     c->ev.resize((size_t)4 * iters);
     for (auto& e : c->ev) DKM_CK(cudaEventCreate(&e));
@@ -498,19 +515,26 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
   cudaError_t e = cudaSuccess;
   do {
     if ((st = zero_run_buffers(c, early != 0)) != DKM_OK) break;
-    if ((e = launch_centroids(A, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream))) break;
-    if (A.stay && (e = launch_cbound(A, 0, c->d, c->stream))) break;
+    if ((e = launch_centroids(A0, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream))) break;
+    if (A0.stay && (e = launch_cbound(A0, 0, c->d, c->stream))) break;
     for (int t = 0; t < iters; ++t) {
       const int par = t & 1;
-      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, cudaEventRecordExternal))) break;
+      // a run returns the SSE of its final labels (computed after the
+      // loop) and the pruning counters of its last pass
+      IterArgs A = A0;
+      A.want_sse = 0;
+      // (an early-stopping run may end on any pass: it counts every pass)
+      A.want_stats = (early || t + 1 == iters) ? 1 : 0;
+      const bool pe = profile && profiled_pass(t, iters);
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, cudaEventRecordExternal))) break;
       if (!brute && (e = launch_search(A, par, c->d, c->stream))) break;
-      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 1], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 1], c->stream, cudaEventRecordExternal))) break;
       if ((e = launch_assign(A, c->d, brute, c->stream))) break;
-      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, cudaEventRecordExternal))) break;
       const int insert = !brute && t + 1 < iters;
       if ((e = launch_centroids(A, 1, t, c->d, nullptr, insert, par ^ 1, nullptr, c->stream))) break;
       if (A.stay && insert && (e = launch_cbound(A, par ^ 1, c->d, c->stream))) break;
-      if (profile && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, cudaEventRecordExternal))) break;
     }
   } while (0);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
@@ -534,6 +558,7 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
   c->g_algo = c->opts.algo;
   c->g_early = early;
   c->g_profile = profile;
+  c->g_args = A0;
   return DKM_OK;
 }
 
@@ -651,7 +676,6 @@ dkm_status apply_tiling(dkm_ctx* c) {
 // tile narrows the unit's list with its own box in k_assign.  unit_g = 1:
 // every tile is its own unit.
 dkm_status apply_units(dkm_ctx* c) {
-  destroy_graph(c);
   DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
   DKM_CK(cudaMemsetAsync(c->tlab, 0xff, sizeof(int) * c->tiles_cap, c->stream));
   if (c->unit_g <= 1) {
@@ -691,10 +715,11 @@ void cloud_boxes(dkm_ctx* c, const std::vector<CloudRun>& hr, std::vector<float>
     }
 }
 
+// The cached run graph stays valid across a setup when the kernel arguments
+// it was captured with come out the same (run_impl compares them).
 dkm_status setup_impl(dkm_ctx* c, const float* points) {
   c->ready = false;
   c->acc_valid = false;
-  destroy_graph(c);
   const float* src = points;
   if (!is_device_ptr(points)) {
     if (!c->pstage) DKM_CK(cudaMalloc(&c->pstage, (size_t)c->n * c->d * sizeof(float)));
@@ -702,7 +727,7 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
                            cudaMemcpyHostToDevice, c->stream));
     src = c->pstage;
   }
-  if (c->opts.profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
+  if (c->opts.profile) DKM_CK(cudaEventRecord(c->ev_s0, c->stream));
   DKM_CK(launch_bbox(src, c->d, c->doff, c->B, c->max_n_b, c->crun, c->st, 0, c->d, c->stream));
   DevState h;
   std::vector<CloudRun> hr;
@@ -742,10 +767,9 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   DKM_CK(cudaStreamSynchronize(c->stream));
   DKM_TRY(apply_tiling(c));
   DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
-  if (c->opts.profile) {
-    DKM_CK(cudaEventRecord(c->ev_b, c->stream));
-    DKM_CK(cudaEventSynchronize(c->ev_b));
-    c->timings.setup_ms = ev_ms(c->ev_a, c->ev_b);
+  if (c->opts.profile) {   // read out lazily (dkm_last_timings), no synchronisation here
+    DKM_CK(cudaEventRecord(c->ev_s, c->stream));
+    c->setup_pending = true;
   }
   c->ready = true;
   return DKM_OK;
@@ -875,7 +899,8 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
                       c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess ||
       cudaEventCreate(&c->ev_a) != cudaSuccess || cudaEventCreate(&c->ev_b) != cudaSuccess ||
-      cudaEventCreate(&c->ev_c) != cudaSuccess) {
+      cudaEventCreate(&c->ev_c) != cudaSuccess || cudaEventCreate(&c->ev_s0) != cudaSuccess ||
+      cudaEventCreate(&c->ev_s) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(DKM_ECUDA, "context initialisation failed"));
   }
@@ -923,20 +948,23 @@ dkm_status run_impl(dkm_ctx* c, const float* init, int max_iter, float* centroid
     return fail(DKM_EINVAL, "max_iter must be in [0, %d] (got %d)", kMaxIterCap, max_iter);
   c->acc_valid = false;
   DKM_TRY(stage_centroids(c, init));
-  DKM_TRY(centroid_box(c, true));
+  // The non-finite check of the initial centroids is read with the run's
+  // final state instead of a synchronisation here; a run on bad centroids
+  // stays in bounds (NaN maps to cell 0) and its outputs are then discarded.
+  DKM_TRY(centroid_box(c, false));
   if (max_iter == 0) {
     DKM_TRY(one_pass(c, false));
     DKM_TRY(export_labels(c, labels_out, false));
     DKM_TRY(export_centroids(c, centroids_out));
     DKM_TRY(read_state(c, h));
+    if (h->bad) return fail(DKM_EINVAL, "centroids contain a non-finite or |x| > 1e18 coordinate");
     DKM_TRY(check_state(*h));
     return DKM_OK;
   }
   DKM_TRY(ensure_hist(c, max_iter));
   const int early = c->opts.early_stop ? 1 : 0;
   const int profile = c->opts.profile ? 1 : 0;
-  if (!c->gexec || c->g_iters != max_iter || c->g_algo != c->opts.algo || c->g_early != early ||
-      c->g_profile != profile)
+  if (!graph_current(c, max_iter, early, profile))
     DKM_TRY(build_run_graph(c, max_iter, early, profile));
   if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
   DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
@@ -948,19 +976,23 @@ dkm_status run_impl(dkm_ctx* c, const float* init, int max_iter, float* centroid
   DKM_TRY(export_centroids(c, centroids_out));
   if (profile) DKM_CK(cudaEventRecord(c->ev_c, c->stream));
   DKM_TRY(read_state(c, h));
+  if (h->bad) return fail(DKM_EINVAL, "centroids contain a non-finite or |x| > 1e18 coordinate");
   DKM_TRY(check_state(*h));
   if (profile) {
     dkm_timings& T = c->timings;
     T.iterations_ms = ev_ms(c->ev_a, c->ev_b);
     T.finalize_ms = ev_ms(c->ev_b, c->ev_c);
-    T.passes = h->passes;
     double s = 0, a = 0, u = 0;
+    int p = 0;
     for (int t = 0; t < h->passes && t < max_iter; ++t) {
+      if (!profiled_pass(t, max_iter)) continue;
       s += ev_ms(c->ev[4 * t + 0], c->ev[4 * t + 1]);
       a += ev_ms(c->ev[4 * t + 1], c->ev[4 * t + 2]);
       u += ev_ms(c->ev[4 * t + 2], c->ev[4 * t + 3]);
+      ++p;
     }
-    int p = h->passes > 0 ? h->passes : 1;
+    T.passes = p;
+    p = p > 0 ? p : 1;
     T.search_ms = (float)(s / p);
     T.assign_ms = (float)(a / p);
     T.update_ms = (float)(u / p);
@@ -1044,8 +1076,7 @@ dkm_tuning current_tuning(const dkm_ctx* c) {
 // warm-up launch.
 dkm_status time_passes(dkm_ctx* c, int passes, float* ms) {
   DKM_TRY(ensure_hist(c, passes));
-  if (!c->gexec || c->g_iters != passes || c->g_algo != c->opts.algo || c->g_early != 0 ||
-      c->g_profile != 0)
+  if (!graph_current(c, passes, 0, 0))
     DKM_TRY(build_run_graph(c, passes, 0, 0));
   DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
   float best = INFINITY;
@@ -1409,8 +1440,13 @@ dkm_status dkm_get_plan(const dkm_ctx* c, dkm_plan_info* out) {
   return DKM_OK;
 }
 
-dkm_status dkm_last_timings(const dkm_ctx* c, dkm_timings* out) {
+dkm_status dkm_last_timings(dkm_ctx* c, dkm_timings* out) {
   if (!c || !out) return fail(DKM_EINVAL, "null argument");
+  if (c->setup_pending) {
+    DKM_CK(cudaEventSynchronize(c->ev_s));
+    c->timings.setup_ms = ev_ms(c->ev_s0, c->ev_s);
+    c->setup_pending = false;
+  }
   *out = c->timings;
   return DKM_OK;
 }
@@ -1437,6 +1473,8 @@ void dkm_destroy(dkm_ctx* c) {
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
   if (c->ev_c) cudaEventDestroy(c->ev_c);
+  if (c->ev_s0) cudaEventDestroy(c->ev_s0);
+  if (c->ev_s) cudaEventDestroy(c->ev_s);
   if (c->arena) cudaFree(c->arena);
   if (c->pstage) cudaFree(c->pstage);
   if (c->lstage) cudaFree(c->lstage);

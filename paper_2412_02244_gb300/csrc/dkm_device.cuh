@@ -152,6 +152,8 @@ struct IterArgs {
   unsigned long long* chg_hist;
   int track_changes;         // read previous labels and count changes
   int early_stop;
+  int want_sse;              // sum the pass SSE (dkm_assign; a run computes its final SSE apart)
+  int want_stats;            // add the pruning counters and fold the pass counters
   int row_filter_min;        // tile lists longer than this are filtered again per row
   int sort_max;              // lists up to this length (<= 32) are sorted, early exit
   // Stay test (the bound layer): cb2[j] = squared distance from centroid j

@@ -148,8 +148,11 @@ struct dkm_ctx {
   // cached iteration graph
   cudaGraphExec_t gexec = nullptr;
   int g_iters = -1, g_algo = -1, g_early = -1, g_profile = -1;
+  dkm::IterArgs g_args{};             // the kernel arguments the graph captured
   std::vector<cudaEvent_t> ev;        // per-pass events of the cached graph
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
+  cudaEvent_t ev_s0 = nullptr, ev_s = nullptr;   // around the last dkm_setup
+  bool setup_pending = false;                    // ev_s not read out yet
 
   dkm_timings timings{};
 };

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
                                                              int32_t* __restrict__ counts_out) {
   // (no kernel-wide early exit: n_done changes inside this kernel, so only
   // the per-cloud pass counts, fixed since k_assign, decide what runs)
-  if (mode == 1 && t >= 0 && blockIdx.x == 0) collect_pass(A, t);
+  if (mode == 1 && t >= 0 && blockIdx.x == 0 && (A.want_stats || A.early_stop))
+    collect_pass(A, t);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= A.k) return;
   const int b = A.kcloud[j];
@@ -267,9 +268,11 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
         if (lane == 0) {
           out[0] = c;
           A.tcnt[t] = 1;
-          Slot& s = A.slots[t & (kSlots - 1)];
-          red_add_u64(&s.cands, 1ull);
-          red_add_u64(&s.stays, 1ull);
+          if (A.want_stats) {
+            Slot& s = A.slots[t & (kSlots - 1)];
+            red_add_u64(&s.cands, 1ull);
+            red_add_u64(&s.stays, 1ull);
+          }
         }
         return;
       }
@@ -421,9 +424,11 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   }
   if (lane == 0) {
     A.tcnt[t] = count;
-    Slot& s = A.slots[t & (kSlots - 1)];
-    red_add_u64(&s.cands, (unsigned long long)count);
-    if (count > kTileCap) red_add_u64(&s.fallback, 1ull);
+    if (A.want_stats) {
+      Slot& s = A.slots[t & (kSlots - 1)];
+      red_add_u64(&s.cands, (unsigned long long)count);
+      if (count > kTileCap) red_add_u64(&s.fallback, 1ull);
+    }
   }
 }
 
@@ -909,7 +914,7 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
       A.lab[i + 1] = lb;
     }
   }
-  sse = tile_sse(best, va, vb, s_sse);
+  if (A.want_sse) sse = tile_sse(best, va, vb, s_sse);
   const int single = accumulate_tile<D>(A, P.x, P.y, P.z, bid, va, vb, s_glob);
   changed = __reduce_add_sync(0xffffffffu, changed);
   if (lane == 0) {
@@ -917,7 +922,7 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
     CloudAcc& ca = A.cacc[b];
     red_add_u64(&ca.sse[t & (kCloudSlots - 1)], (unsigned long long)sse);
     if (changed) red_add_u64(&ca.changed[t & (kCloudSlots - 1)], (unsigned long long)changed);
-    red_add_u64(&A.slots[t & (kSlots - 1)].evals, evals);
+    if (A.want_stats) red_add_u64(&A.slots[t & (kSlots - 1)].evals, evals);
   }
 }
 
