@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
 // CTAs free their SM slot as soon as their own tiles are done.
 // ---------------------------------------------------------------------------
 #ifndef DKM_ASSIGN_WARPS
-#define DKM_ASSIGN_WARPS 2
+#define DKM_ASSIGN_WARPS 1   // one-warp CTAs: 24 per SM, freed as soon as their tile is done
 #endif
 constexpr int kAssignWarps = DKM_ASSIGN_WARPS;
 #ifndef DKM_ASSIGN_MIN_WARPS
@@ -474,13 +474,17 @@ __device__ __forceinline__ void take_min(float s, int id, float& best, int& bid)
   }
 }
 
+#ifndef DKM_EVAL_UNROLL
+#define DKM_EVAL_UNROLL 1
+#endif
+constexpr int kEvalUnroll = DKM_EVAL_UNROLL;   // candidates per unrolled step
 // all rows of the tile against candidates s_c[idx[j]] (idx == nullptr: s_c[j])
 template <int D>
 __device__ __forceinline__ void eval_list(const float4* __restrict__ s_c,
                                           const unsigned short* __restrict__ idx, int m,
                                           const Pts<D>& P, float2 (&best)[kRowsPerWarp],
                                           int2 (&bid)[kRowsPerWarp]) {
-#pragma unroll 2
+#pragma unroll kEvalUnroll
   for (int j = 0; j < m; ++j) {
     const float4 c = s_c[idx ? idx[j] : j];
     const int id = __float_as_int(c.w);
