@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "c2e60855d00e45d3", "bytes_per_launch": 134_206_464 + 22_245_120,
+NCU_TRAFFIC = {"sha": "37c5c7b6d6a38189", "bytes_per_launch": 134_326_528 + 21_208_320,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
@@ -348,6 +348,8 @@ def run_ours(args):
                                    stream=stream.cuda_stream)
     torch.cuda.synchronize()
     ctx = dkm.dkm_create(pts, n, d, k, opts)
+    # index settings measured by the autotuner, once, before the warm-up
+    tune = dkm.dkm_autotune(ctx, init, passes=3, use_cache=False) if args.tune else None
 
     def step():
         dkm.dkm_setup(ctx, pts)
@@ -418,6 +420,8 @@ def run_ours(args):
         Tb = dkm.dkm_last_timings(cb)
         oi = dkm.dkm_default_options(early_stop=0, profile=1, stream=stream.cuda_stream)
         ci = dkm.dkm_create(pts, n, d, k, oi)
+        if tune is not None:
+            dkm.dkm_set_tuning(ci, tune)
         dkm.dkm_run(ci, C, 2, Cb, lb)
         dkm.dkm_run(ci, C, 2, Cb, lb)
         Ti = dkm.dkm_last_timings(ci)
@@ -457,6 +461,14 @@ def run_ours(args):
                                  "hbm_frac_of_iteration": n * ASSIGN_BYTES_PER_POINT
                                  / (per_iter * 1e-3) / 1e9 / hbm,
                                  "setup_ms": float(np.mean(setup_ms))}
+    if tune is not None:
+        line["tuning"] = {"cells_per_centroid": tune.cells_per_centroid,
+                          "tile_cut_div": tune.tile_cut_div,
+                          "row_filter_min": tune.row_filter_min, "sort_max": tune.sort_max,
+                          "tile_group": tune.tile_group, "stay_test": tune.stay_test,
+                          "ms_per_pass": tune.ms_per_pass,
+                          "ms_per_pass_default": tune.ms_per_pass_before, "trials": tune.trials,
+                          "note": "chosen by dkm_autotune before the warm-up, outside the timed region"}
     line["pruning"] = {"evals_per_point": stats.evals_per_point,
                        "candidates_per_tile": stats.candidates_per_tile,
                        "fallback_tiles": stats.fallback_tiles,
@@ -501,6 +513,8 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-brute", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="run dkm_autotune on the workload before the warm-up (0 = defaults)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched-cloud and differentiable side measurements")
     args = ap.parse_args(argv)

@@ -297,3 +297,22 @@ def test_sse_history_non_increasing(dkm):
         assert sse <= prev * (1 + 1e-6)
         prev = sse
         C, _ = gpu_update(dkm, ctx, None, C)
+
+
+def test_run_graph_reuse_across_setups(dkm):
+    """A run after re-running dkm_setup equals a fresh context bit for bit,
+    whether the cached run graph is kept (same points) or rebuilt (new
+    points of the same size)."""
+    a = synth.lidar3d(seed=71, n=50_003, k=70, n_objects=20)
+    b = synth.lidar3d(seed=72, n=50_003, k=70, n_objects=25)
+    ctx = make_ctx(dkm, a.points, a.k, early_stop=0)
+    first = gpu_run(dkm, ctx, a.init, 7)
+    dkm.dkm_setup(ctx, dev(a.points))
+    again = gpu_run(dkm, ctx, a.init, 7)
+    for x, y in zip(first, again):
+        assert np.array_equal(x, y)
+    dkm.dkm_setup(ctx, dev(b.points))
+    moved = gpu_run(dkm, ctx, b.init, 7)
+    fresh = gpu_run(dkm, make_ctx(dkm, b.points, b.k, early_stop=0), b.init, 7)
+    for x, y in zip(moved, fresh):
+        assert np.array_equal(x, y)
