@@ -258,7 +258,7 @@ typedef struct {
      * (0, max(4, opts.cells_per_centroid)] */
     float cells_per_centroid;
     /* a cloud's tiles are cut at the finest Morton cubes that add at most
-     * its 256-point windows / tile_cut_div tiles; 2 .. 1024 (default 8) */
+     * its 256-point windows / tile_cut_div tiles; 1 .. 1024 (default 8) */
     int tile_cut_div;
     /* tile candidate lists longer than this are filtered again per row of
      * 64 points (default 48; >= 256 turns the row filter off) */
@@ -298,7 +298,7 @@ DKM_API dkm_status dkm_set_tuning(dkm_ctx* ctx, const dkm_tuning* tuning);
 /*
  * Measure and apply the fastest setting for this context: coordinate
  * descent over cells_per_centroid {0.5, 1, 2, 4}, tile_cut_div
- * {2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256}, sort_max
+ * {1, 2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256}, sort_max
  * {0, 16, 32}, tile_group {1, 2, 4, 8, 16} and stay_test {0, 1}, each
  * setting timed (CUDA events, best of two) over `passes` Lloyd passes
  * (1 .. 64, no early stop) from init_centroids.  The context's labels and

@@ -50,7 +50,7 @@ constexpr size_t kDefaultBudget = size_t(64) << 20;
 constexpr int64_t kMaxPoints = (int64_t(1) << 31) - kBlockPts;
 constexpr int kMaxClouds = 65535;        // grid.y limit of the per-cloud box kernel
 constexpr float kTuneMaxCpc = 4.0f;      // densest grid the arena is sized for
-constexpr int kMinCutDiv = 2;            // most tile cuts the arena is sized for
+constexpr int kMinCutDiv = 1;            // most tile cuts the arena is sized for
 
 // true for memory a kernel may dereference directly (device or managed)
 bool is_device_ptr(const void* p) {
@@ -1157,7 +1157,7 @@ dkm_status autotune_impl(dkm_ctx* c, const float* init, int passes, int use_cach
     t.cells_per_centroid = v;
     DKM_TRY(trial(t));
   }
-  for (int v : {2, 4, 8, 16, 32}) {
+  for (int v : {1, 2, 4, 8, 16, 32}) {
     if (v == best.tile_cut_div) continue;
     dkm_tuning t = best;
     t.tile_cut_div = v;

@@ -153,7 +153,7 @@ def test_batched_stats_and_plan(dkm):
     gpu_assign(dkm, ctx, init)
     st = dkm.dkm_last_stats(ctx)
     windows = -(-P.shape[0] // 256)
-    assert windows <= st.tiles <= windows + windows // 2 + 3 * len(ks) + 2
+    assert windows <= st.tiles <= windows + windows // 8 + 3 * len(ks) + 2
     assert st.evals_per_point >= 1.0
     plan = dkm.dkm_get_plan(ctx)
     assert plan.cells >= len(ks)
@@ -200,7 +200,7 @@ def test_batched_uneven_workload_full_size(dkm, oracle):
 
 
 @pytest.mark.parametrize("setting", [dict(cells_per_centroid=0.5), dict(cells_per_centroid=4.0),
-                                     dict(tile_cut_div=2), dict(tile_cut_div=32),
+                                     dict(tile_cut_div=1), dict(tile_cut_div=32),
                                      dict(row_filter_min=16), dict(row_filter_min=256),
                                      dict(sort_max=32), dict(sort_max=16),
                                      dict(tile_group=4), dict(tile_group=32),
@@ -235,7 +235,7 @@ def test_autotune_choice_cache_and_exactness(dkm):
     assert t.from_cache == 0 and t.trials >= 10
     assert 0 < t.ms_per_pass <= t.ms_per_pass_before
     assert t.cells_per_centroid in (0.5, 1.0, 2.0, 4.0)
-    assert t.tile_cut_div in (2, 4, 8, 16, 32) and t.row_filter_min in (16, 32, 48, 96, 256)
+    assert t.tile_cut_div in (1, 2, 4, 8, 16, 32) and t.row_filter_min in (16, 32, 48, 96, 256)
     assert t.sort_max in (0, 16, 32) and t.tile_group in (1, 2, 4, 8, 16)
     assert t.stay_test in (0, 1)
     cur = dkm.dkm_get_tuning(ctx)
@@ -254,7 +254,7 @@ def test_tuning_rejects_bad_values(dkm):
     P, off, ks, coff, init = _small(3, seed=55, n_clouds=3)
     ctx = _ctx(dkm, P, off, ks)
     for kw in (dict(cells_per_centroid=0.0), dict(cells_per_centroid=100.0),
-               dict(tile_cut_div=1), dict(row_filter_min=-1), dict(sort_max=33),
+               dict(tile_cut_div=0), dict(row_filter_min=-1), dict(sort_max=33),
                dict(tile_group=0), dict(tile_group=33), dict(stay_test=2)):
         with pytest.raises(dkm.DkmError) as e:
             dkm.dkm_set_tuning(ctx, **kw)
