@@ -19,7 +19,7 @@
  *   - Algorithm 1 ("Refine centroid": c_j <- sv(j)/|S_j|): the refine step is
  *     the cluster mean.
  *
- * Readings where the paper is silent (each is also listed in the design doc):
+ * Readings where the paper is silent:
  *   - ties go to the lowest centroid index (scan j = 0..k-1 with strict <);
  *   - an empty cluster keeps its previous centroid (sv/|S| is undefined);
  *   - "converged" = an assignment pass that changes no label;

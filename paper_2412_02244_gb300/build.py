@@ -3,7 +3,7 @@
 Each .cu translation unit compiles in its own nvcc process (in parallel),
 then one nvcc -shared links them.  The CUDA runtime is linked statically,
 so the library loads on machines without a GPU (symbol checks) and shares
-the driver's primary context with PyTorch on machines with one.
+the CUDA driver's primary context with PyTorch on machines with one.
 """
 from __future__ import annotations
 
