@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "37c5c7b6d6a38189", "bytes_per_launch": 134_326_528 + 21_208_320,
+NCU_TRAFFIC = {"sha": "37c5c7b6d6a38189", "bytes_per_launch": 132_628_480 + 22_285_056,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
@@ -190,6 +190,51 @@ def launches_per_step(iters: int) -> int:
     # iters x (search, assign, centroids); finalize, collect, export
     run = 3 + 2 + 3 * iters + 3
     return setup + run
+
+
+DEFAULT_TUNING = dict(cells_per_centroid=1.0, tile_cut_div=8, row_filter_min=48, sort_max=0,
+                      tile_group=1, stay_test=0)
+ABLATIONS = [
+    ("stay_test (bound layer)", {"stay_test": 1}),
+    ("tile_group 4 (hierarchical tiles)", {"tile_group": 4}),
+    ("tile_group 8 (hierarchical tiles)", {"tile_group": 8}),
+    ("sort_max 32 (sorted early exit)", {"sort_max": 32}),
+    ("row_filter_min 48 (per-row refilter)", {"row_filter_min": 48}),
+    ("tile_cut_div 8 (coarser tiles)", {"tile_cut_div": 8}),
+    ("cells_per_centroid 2", {"cells_per_centroid": 2.0}),
+]
+
+
+def bench_ablations(dkm, pts, n, d, k, C, stream, tune):
+    """Per-pass time of one Lloyd pass from the given centroids under each
+    setting (the tuned one, then single changes from it)."""
+    import torch
+    o = dkm.dkm_default_options(early_stop=0, profile=1, stream=stream.cuda_stream)
+    ctx = dkm.dkm_create(pts, n, d, k, o)
+    base = dkm.dkm_get_tuning(ctx) if tune is None else tune
+    C2 = torch.empty_like(C)
+    lab = torch.empty(n, dtype=torch.int32, device=pts.device)
+    out = []
+    for name, change in [("tuned", {})] + ABLATIONS + [("defaults", DEFAULT_TUNING)]:
+        t = dkm.dkm_tuning()
+        for f, _ in dkm.dkm_tuning._fields_:
+            setattr(t, f, getattr(base, f))
+        for key, v in change.items():
+            setattr(t, key, v)
+        dkm.dkm_set_tuning(ctx, t)
+        ms = []
+        for _ in range(3):
+            dkm.dkm_run(ctx, C, 1, C2, lab)
+            T = dkm.dkm_last_timings(ctx)
+            ms.append(T.search_ms + T.assign_ms + T.update_ms)
+        st = dkm.dkm_last_stats(ctx)
+        out.append({"setting": name, "ms_per_pass": float(np.median(ms[1:])),
+                    "evals_per_point": st.evals_per_point,
+                    "candidates_per_tile": st.candidates_per_tile, "tiles": st.tiles,
+                    "stayed_tiles": st.stayed_tiles})
+    ctx.close()
+    return {"from": "one pass from the timed run's final centroids per setting",
+            "settings": out}
 
 
 BATCHED = dict(workload="batched3d", clouds=512, n_i="round(2^U[10,17])",
@@ -348,8 +393,18 @@ def run_ours(args):
                                    stream=stream.cuda_stream)
     torch.cuda.synchronize()
     ctx = dkm.dkm_create(pts, n, d, k, opts)
-    # index settings measured by the autotuner, once, before the warm-up
-    tune = dkm.dkm_autotune(ctx, init, passes=3, use_cache=False) if args.tune else None
+    # index settings measured by the autotuner, once, before the warm-up, or
+    # given explicitly (--set, e.g. to profile the tuned configuration)
+    tune = None
+    if args.set:
+        kw = {}
+        for item in args.set.split(","):
+            key, v = item.split("=")
+            kw[key] = float(v) if key == "cells_per_centroid" else int(v)
+        dkm.dkm_set_tuning(ctx, **kw)
+        tune = dkm.dkm_get_tuning(ctx)
+    elif args.tune:
+        tune = dkm.dkm_autotune(ctx, init, passes=3, use_cache=False)
 
     def step():
         dkm.dkm_setup(ctx, pts)
@@ -433,6 +488,12 @@ def run_ours(args):
         cb.close()
         ci.close()
 
+    # measured effect of each index option on this workload: one pass from
+    # the run's final centroids per setting, on a fresh context
+    ablations = None
+    if rank == 0 and not args.no_extra:
+        ablations = bench_ablations(dkm, pts, n, d, k, C, stream, tune)
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -468,7 +529,9 @@ def run_ours(args):
                           "tile_group": tune.tile_group, "stay_test": tune.stay_test,
                           "ms_per_pass": tune.ms_per_pass,
                           "ms_per_pass_default": tune.ms_per_pass_before, "trials": tune.trials,
-                          "note": "chosen by dkm_autotune before the warm-up, outside the timed region"}
+                          "note": ("given with --set" if args.set else
+                                   "chosen by dkm_autotune before the warm-up, outside the "
+                                   "timed region")}
     line["pruning"] = {"evals_per_point": stats.evals_per_point,
                        "candidates_per_tile": stats.candidates_per_tile,
                        "fallback_tiles": stats.fallback_tiles,
@@ -489,6 +552,8 @@ def run_ours(args):
                                           f"against all k=10000 centroids + update) of "
                                           f"{min(args.cpu_sample, n)} of the workload's {n} "
                                           f"points ({dt:.1f} s)"}
+    if ablations:
+        line["ablations"] = ablations
     if ws == 1 and not args.no_extra:
         ctx.close()
         line["batched"] = bench_batched(dkm, torch, dev, stream, max(2, min(args.steps, 5)), hbm)
@@ -515,6 +580,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune", type=int, default=1,
                     help="run dkm_autotune on the workload before the warm-up (0 = defaults)")
+    ap.add_argument("--set", default="",
+                    help="explicit index settings instead of the autotuner, e.g. "
+                         "tile_cut_div=1,row_filter_min=256")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched-cloud and differentiable side measurements")
     args = ap.parse_args(argv)
