@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
 #endif
 constexpr int kAssignWarps = DKM_ASSIGN_WARPS;
 #ifndef DKM_ASSIGN_MIN_WARPS
-#define DKM_ASSIGN_MIN_WARPS 24
+#define DKM_ASSIGN_MIN_WARPS 32   // 64 registers: 32 one-warp CTAs per SM
 #endif
 template <int D>
 struct Pts {
