@@ -339,12 +339,14 @@ def bench_soft(dkm, torch, dev, stream, steps: int):
     gp = torch.empty_like(P)
     gi = torch.empty_like(init)
     gc = torch.empty_like(init)
+    stats = torch.empty((T, 2, P.shape[0]), dtype=torch.float32, device=dev)
+    norms = torch.empty((T, B, k), dtype=torch.float32, device=dev)
     dl = np.ones(B)
     s = stream.cuda_stream
 
     def fwd_bwd():
-        dkm.dkm_soft_forward(P, off, B, 3, k, init, T, tau, ck, loss, s)
-        dkm.dkm_soft_backward(P, off, B, 3, k, ck, T, tau, dl, gp, gi, s)
+        dkm.dkm_soft_forward(P, off, B, 3, k, init, T, tau, ck, loss, s, stats=stats, norms=norms)
+        dkm.dkm_soft_backward(P, off, B, 3, k, ck, T, tau, dl, gp, gi, s, stats=stats, norms=norms)
 
     def hard():
         dkm.dkm_hard_sse(P, off, B, 3, k, init, None, loss, gp, gc, s)

@@ -349,19 +349,27 @@ DKM_API void dkm_destroy(dkm_ctx* ctx);
  *   loss[b] = sum_ij w^T_ij ||p_i - c^T_j||^2.
  * dkm_soft_forward writes the centroids of every step into ckpt
  * (B x (T+1) x k x d, step-major: ckpt[t] is B x k x d) and the loss.
- * dkm_soft_backward takes those checkpoints and the upstream gradient
+ * Optionally (both device pointers, nullable) it also keeps per step the
+ * two softmax statistics of every point, stats (T x 2 x n_total floats:
+ * min_j ||p_i - c^t_j||^2, then 1 / the softmax normaliser), and the
+ * weight sums of every centroid, norms (T x B x k floats) -- O(n) per step,
+ * not the n x k weights.
+ * dkm_soft_backward takes the checkpoints and the upstream gradient
  * dloss[b] = dOut/dloss[b] and writes dOut/dpoints (n_total x d) and
  * dOut/dinit_centroids (B x k x d), recomputing the weights of each step
- * from ckpt instead of storing them.  tau is a constant of the loss.
+ * from ckpt instead of storing them; given the forward's stats and norms
+ * (both, else neither) it skips recomputing them, with the same result
+ * bit for bit.  tau is a constant of the loss.
  * Errors: DKM_EINVAL (sizes, offsets, null pointers), DKM_ECUDA.
  */
 DKM_API dkm_status dkm_soft_forward(const float* points, const int64_t* offsets, int B, int d,
                                     int k, const float* init_centroids, int T, const float* tau,
-                                    float* ckpt, double* loss, void* stream);
+                                    float* ckpt, double* loss, float* stats, float* norms,
+                                    void* stream);
 DKM_API dkm_status dkm_soft_backward(const float* points, const int64_t* offsets, int B, int d,
                                      int k, const float* ckpt, int T, const float* tau,
-                                     const double* dloss, float* grad_points, float* grad_init,
-                                     void* stream);
+                                     const double* dloss, const float* stats, const float* norms,
+                                     float* grad_points, float* grad_init, void* stream);
 
 /*
  * Hard SSE of each cloud, Eq. 1 with the nearest centroid (lowest index on

@@ -47,19 +47,26 @@ class SoftKMeansLoss(torch.autograd.Function):
         tau = tau.to(torch.float32).cpu().contiguous()
         ckpt = torch.empty((T + 1, B, k, d), dtype=torch.float32, device=points.device)
         loss = torch.empty(B, dtype=torch.float64, device=points.device)
-        dkm.dkm_soft_forward(points, offsets, B, d, k, init, T, tau, ckpt, loss, _stream())
-        ctx.save_for_backward(points, ckpt)
+        # per-step softmax statistics (O(n) per step) so the backward need not
+        # recompute them; the n x k weights are never stored
+        n_total = points.shape[0]
+        stats = torch.empty((T, 2, n_total), dtype=torch.float32, device=points.device)
+        norms = torch.empty((T, B, k), dtype=torch.float32, device=points.device)
+        dkm.dkm_soft_forward(points, offsets, B, d, k, init, T, tau, ckpt, loss, _stream(),
+                             stats=stats, norms=norms)
+        ctx.save_for_backward(points, ckpt, stats, norms)
         ctx.meta = (offsets, tau, int(T), B, k, d)
         return loss
 
     @staticmethod
     def backward(ctx, gloss):
-        points, ckpt = ctx.saved_tensors
+        points, ckpt, stats, norms = ctx.saved_tensors
         offsets, tau, T, B, k, d = ctx.meta
         gp = torch.empty_like(points)
         gi = torch.empty((B, k, d), dtype=torch.float32, device=points.device)
         dl = gloss.detach().to(torch.float64).contiguous()
-        dkm.dkm_soft_backward(points, offsets, B, d, k, ckpt, T, tau, dl, gp, gi, _stream())
+        dkm.dkm_soft_backward(points, offsets, B, d, k, ckpt, T, tau, dl, gp, gi, _stream(),
+                              stats=stats, norms=norms)
         return gp, gi, None, None, None
 
 

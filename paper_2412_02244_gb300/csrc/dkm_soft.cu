@@ -42,6 +42,7 @@ struct SoftArgs {
   float* iz;              // per point: 1 / sum_j exp((m - D_ij) / tau)
   float* aux;             // per point: rho_i (soft step) or E_i (loss stage)
   double* part;           // B x ns x k x 4 column partials
+  int use_stats;          // kRowStep: m and iz given (from the forward), not recomputed
 };
 
 enum RowMode { kRowStats = 0, kRowLoss = 1, kRowStep = 2, kRowLossBwd = 3, kRowHard = 4 };
@@ -122,11 +123,19 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
       }
     }
   } else {
-    float m = INFINITY;
-    for (int j = 0; j < k; ++j) m = fminf(m, sqd<D>(p, sc[j], dv));
-    float z = 0.f;
-    for (int j = 0; j < k; ++j) z += expf((m - sqd<D>(p, sc[j], dv)) * it);
-    const float iz = 1.f / z;
+    const bool given = MODE == kRowStep && A.use_stats;
+    float m = INFINITY, iz = 0.f;
+    if (given) {   // the forward's statistics of this step (same values, bit for bit)
+      if (valid) {
+        m = A.m[i];
+        iz = A.iz[i];
+      }
+    } else {
+      for (int j = 0; j < k; ++j) m = fminf(m, sqd<D>(p, sc[j], dv));
+      float z = 0.f;
+      for (int j = 0; j < k; ++j) z += expf((m - sqd<D>(p, sc[j], dv)) * it);
+      iz = 1.f / z;
+    }
     if (MODE == kRowLoss || MODE == kRowLossBwd) {
       // E = sum_j w D;  B = sum_j w (p - c);  F = sum_j w D (p - c)
       float E = 0.f;
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
         A.aux[i] = rho;
       }
     }
-    if (valid) {
+    if (valid && !given) {
       A.m[i] = m;
       A.iz[i] = iz;
     }
@@ -451,9 +460,22 @@ dkm_status finish_loss(const SoftScratch& S, const SoftPlan& P, int B, double* l
   return DKM_OK;
 }
 
+// the scratch with the row statistics of step t in the caller's arrays
+// (stats: T x [m | iz] x n_total)
+SoftScratch step_scratch(const SoftScratch& S, const SoftPlan& P, const float* stats, int t) {
+  SoftScratch St = S;
+  if (stats) {
+    const size_t n = (size_t)P.n_total;
+    St.A.m = const_cast<float*>(stats) + (size_t)(2 * t) * n;
+    St.A.iz = const_cast<float*>(stats) + (size_t)(2 * t + 1) * n;
+  }
+  return St;
+}
+
 template <int D>
 dkm_status soft_forward_impl(const float* pts, const SoftPlan& P, int B, int k, const float* init,
-                             int T, const float* tau, float* ckpt, double* loss, cudaStream_t st) {
+                             int T, const float* tau, float* ckpt, double* loss, float* stats,
+                             float* norms, cudaStream_t st) {
   SoftScratch S;
   dkm_status r = soft_alloc(P, B, D, k, tau, st, &S);
   if (r != DKM_OK) return r;
@@ -462,9 +484,11 @@ dkm_status soft_forward_impl(const float* pts, const SoftPlan& P, int B, int k, 
   SOFT_CK(cudaMemcpyAsync(ckpt, init, sizeof(float) * ck, cudaMemcpyDefault, st));
   for (int t = 0; t < T; ++t) {
     const float* Ct = ckpt + t * ck;
-    launch_row<D, kRowStats>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    launch_col<D, kColMean>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    launch_reduce(S, D, 0, Ct, ckpt + (t + 1) * ck, nullptr, nullptr, st);
+    const SoftScratch St = step_scratch(S, P, stats, t);
+    launch_row<D, kRowStats>(St, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_col<D, kColMean>(St, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_reduce(St, D, 0, Ct, ckpt + (t + 1) * ck, norms ? norms + (size_t)t * B * k : nullptr,
+                  nullptr, st);
   }
   launch_row<D, kRowLoss>(S, P, ckpt + T * ck, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                           st);
@@ -478,8 +502,8 @@ dkm_status soft_forward_impl(const float* pts, const SoftPlan& P, int B, int k, 
 
 template <int D>
 dkm_status soft_backward_impl(const float* pts, const SoftPlan& P, int B, int k, const float* ckpt,
-                              int T, const float* tau, const double* dloss, float* gp, float* gi,
-                              cudaStream_t st) {
+                              int T, const float* tau, const double* dloss, const float* stats,
+                              const float* norms, float* gp, float* gi, cudaStream_t st) {
   SoftScratch S;
   dkm_status r = soft_alloc(P, B, D, k, tau, st, &S);
   if (r != DKM_OK) return r;
@@ -494,15 +518,24 @@ dkm_status soft_backward_impl(const float* pts, const SoftPlan& P, int B, int k,
   int cur = 0;
   launch_reduce(S, D, 1, CT, nullptr, nullptr, S.G[cur], st);
   // the updates, last first
+  const bool given = stats && norms;   // the forward's per-step statistics
   for (int t = T - 1; t >= 0; --t) {
     const float* Ct = ckpt + t * ck;
     const float* Cn = ckpt + (t + 1) * ck;
-    launch_row<D, kRowStats>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    launch_col<D, kColMean>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    launch_reduce(S, D, 0, Ct, nullptr, S.N, nullptr, st);
-    launch_row<D, kRowStep>(S, P, Ct, Cn, S.N, S.G[cur], nullptr, gp, nullptr, st);
-    launch_col<D, kColStep>(S, P, Ct, Cn, S.N, S.G[cur], nullptr, nullptr, st);
-    launch_reduce(S, D, 1, Ct, nullptr, nullptr, S.G[cur ^ 1], st);
+    SoftScratch St = S;
+    const float* N = S.N;
+    if (given) {
+      St = step_scratch(S, P, stats, t);
+      St.A.use_stats = 1;
+      N = norms + (size_t)t * B * k;
+    } else {
+      launch_row<D, kRowStats>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+      launch_col<D, kColMean>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+      launch_reduce(S, D, 0, Ct, nullptr, S.N, nullptr, st);
+    }
+    launch_row<D, kRowStep>(St, P, Ct, Cn, N, S.G[cur], nullptr, gp, nullptr, st);
+    launch_col<D, kColStep>(St, P, Ct, Cn, N, S.G[cur], nullptr, nullptr, st);
+    launch_reduce(St, D, 1, Ct, nullptr, nullptr, S.G[cur ^ 1], st);
     cur ^= 1;
   }
   SOFT_CK(cudaMemcpyAsync(gi, S.G[cur], sizeof(float) * ck, cudaMemcpyDefault, st));
@@ -543,21 +576,24 @@ extern "C" {
 
 DKM_API dkm_status dkm_soft_forward(const float* points, const int64_t* offsets, int B, int d,
                                     int k, const float* init_centroids, int T, const float* tau,
-                                    float* ckpt, double* loss, void* stream) {
+                                    float* ckpt, double* loss, float* stats, float* norms,
+                                    void* stream) {
   SoftPlan P;
   dkm_status r = soft_plan(offsets, B, d, k, &P);
   if (r != DKM_OK) return r;
   if (T < 0) return soft_fail(DKM_EINVAL, "T must be >= 0");
   if (!points || !init_centroids || !tau || !ckpt) return soft_fail(DKM_EINVAL, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
-  return d == 3 ? soft_forward_impl<3>(points, P, B, k, init_centroids, T, tau, ckpt, loss, st)
-                : soft_forward_impl<2>(points, P, B, k, init_centroids, T, tau, ckpt, loss, st);
+  return d == 3 ? soft_forward_impl<3>(points, P, B, k, init_centroids, T, tau, ckpt, loss, stats,
+                                       norms, st)
+                : soft_forward_impl<2>(points, P, B, k, init_centroids, T, tau, ckpt, loss, stats,
+                                       norms, st);
 }
 
 DKM_API dkm_status dkm_soft_backward(const float* points, const int64_t* offsets, int B, int d,
                                      int k, const float* ckpt, int T, const float* tau,
-                                     const double* dloss, float* grad_points, float* grad_init,
-                                     void* stream) {
+                                     const double* dloss, const float* stats, const float* norms,
+                                     float* grad_points, float* grad_init, void* stream) {
   SoftPlan P;
   dkm_status r = soft_plan(offsets, B, d, k, &P);
   if (r != DKM_OK) return r;
@@ -565,10 +601,10 @@ DKM_API dkm_status dkm_soft_backward(const float* points, const int64_t* offsets
   if (!points || !ckpt || !tau || !dloss || !grad_points || !grad_init)
     return soft_fail(DKM_EINVAL, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
-  return d == 3 ? soft_backward_impl<3>(points, P, B, k, ckpt, T, tau, dloss, grad_points,
-                                        grad_init, st)
-                : soft_backward_impl<2>(points, P, B, k, ckpt, T, tau, dloss, grad_points,
-                                        grad_init, st);
+  return d == 3 ? soft_backward_impl<3>(points, P, B, k, ckpt, T, tau, dloss, stats, norms,
+                                        grad_points, grad_init, st)
+                : soft_backward_impl<2>(points, P, B, k, ckpt, T, tau, dloss, stats, norms,
+                                        grad_points, grad_init, st);
 }
 
 DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int B, int d, int k,

@@ -121,11 +121,12 @@ _SIGS = [
     ("dkm_soft_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                        ctypes.c_void_p]),
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("dkm_soft_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p, ctypes.c_void_p]),
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     ("dkm_hard_sse", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -398,8 +399,9 @@ def dkm_destroy(ctx: Context) -> None:
 
 
 def dkm_soft_forward(points, offsets, B: int, d: int, k: int, init_centroids, T: int, tau, ckpt,
-                     loss, stream: int = 0) -> None:
-    """Soft k-means loss of B clouds; fills ckpt ((T+1) x B x k x d) and loss (B)."""
+                     loss, stream: int = 0, stats=None, norms=None) -> None:
+    """Soft k-means loss of B clouds; fills ckpt ((T+1) x B x k x d) and loss (B), and
+    optionally the per-step statistics stats (T x 2 x n_total) and norms (T x B x k)."""
     off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
     n_total = int(offsets[-1])
     p, _k1 = _arr(points, "float32", n_total * d, "points")
@@ -407,12 +409,14 @@ def dkm_soft_forward(points, offsets, B: int, d: int, k: int, init_centroids, T:
     tv, _k3 = _arr(tau, "float32", B, "tau")
     ck, _k4 = _arr(ckpt, "float32", (T + 1) * B * k * d, "ckpt")
     ls, _k5 = _arr(loss, "float64", B, "loss")
-    _check(lib().dkm_soft_forward(p, off, B, d, k, c0, int(T), tv, ck, ls,
+    sv, _k6 = _arr(stats, "float32", T * 2 * n_total, "stats")
+    nv, _k7 = _arr(norms, "float32", T * B * k, "norms")
+    _check(lib().dkm_soft_forward(p, off, B, d, k, c0, int(T), tv, ck, ls, sv, nv,
                                   ctypes.c_void_p(stream or 0)), "dkm_soft_forward")
 
 
 def dkm_soft_backward(points, offsets, B: int, d: int, k: int, ckpt, T: int, tau, dloss,
-                      grad_points, grad_init, stream: int = 0) -> None:
+                      grad_points, grad_init, stream: int = 0, stats=None, norms=None) -> None:
     off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
     n_total = int(offsets[-1])
     p, _k1 = _arr(points, "float32", n_total * d, "points")
@@ -421,7 +425,9 @@ def dkm_soft_backward(points, offsets, B: int, d: int, k: int, ckpt, T: int, tau
     dl, _k4 = _arr(dloss, "float64", B, "dloss")
     gp, _k5 = _arr(grad_points, "float32", n_total * d, "grad_points")
     gi, _k6 = _arr(grad_init, "float32", B * k * d, "grad_init")
-    _check(lib().dkm_soft_backward(p, off, B, d, k, ck, int(T), tv, dl, gp, gi,
+    sv, _k7 = _arr(stats, "float32", T * 2 * n_total, "stats")
+    nv, _k8 = _arr(norms, "float32", T * B * k, "norms")
+    _check(lib().dkm_soft_backward(p, off, B, d, k, ck, int(T), tv, dl, sv, nv, gp, gi,
                                    ctypes.c_void_p(stream or 0)), "dkm_soft_backward")
 
 

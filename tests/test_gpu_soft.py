@@ -170,3 +170,30 @@ def test_soft_errors(dkm):
         dkm.dkm_soft_forward(P, np.array([0, 10, 10], np.int64), 2, 3, 2, init, 1,
                              np.ones(2, np.float32), ck, loss)
     assert e.value.status == dkm.DKM_EINVAL
+
+
+def test_soft_backward_with_forward_statistics_is_identical(dkm):
+    """The backward given the forward's per-step statistics returns exactly
+    the gradient it computes without them."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(81)
+    clouds = [synth.gaussian_mixture_3d(n, 6, rng) for n in (900, 2500 + 3)]
+    pts, P, init, off, tau = _batch(clouds, 16, 82)
+    B, k, d = init.shape
+    T = 4
+    Pt = torch.from_numpy(P).cuda()
+    It = torch.from_numpy(init).cuda()
+    ck = torch.empty((T + 1, B, k, d), dtype=torch.float32, device="cuda")
+    loss = torch.empty(B, dtype=torch.float64, device="cuda")
+    st = torch.empty((T, 2, P.shape[0]), dtype=torch.float32, device="cuda")
+    nm = torch.empty((T, B, k), dtype=torch.float32, device="cuda")
+    dkm.dkm_soft_forward(Pt, off, B, d, k, It, T, tau, ck, loss, stats=st, norms=nm)
+    dl = np.array([0.7, -1.3])
+    out = []
+    for kw in (dict(), dict(stats=st, norms=nm)):
+        gp = torch.empty_like(Pt)
+        gi = torch.empty_like(It)
+        dkm.dkm_soft_backward(Pt, off, B, d, k, ck, T, tau, dl, gp, gi, **kw)
+        out.append((gp.cpu().numpy(), gi.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.all(nm.cpu().numpy() > 0)
