@@ -1025,14 +1025,26 @@ dkm_status apply_tuning(dkm_ctx* c, const dkm_tuning& t) {
   DKM_TRY(tuning_check(c, t));
   bool changed = false;
   if (t.cells_per_centroid != c->cpc) {
+    const float old = c->cpc;
     c->cpc = t.cells_per_centroid;
-    DKM_TRY(plan_clouds(c, c->h_blo, c->h_bhi));
+    dkm_status r = plan_clouds(c, c->h_blo, c->h_bhi);
+    if (r != DKM_OK) {   // keep the context on its previous, valid grids
+      const std::string msg = dkm_last_error();
+      c->cpc = old;
+      plan_clouds(c, c->h_blo, c->h_bhi);
+      dkm_set_last_error(msg.c_str());
+      return r;
+    }
     DKM_TRY(upload_clouds(c));
     changed = true;
   }
   if (t.tile_cut_div != c->cut_div) {
     c->cut_div = t.tile_cut_div;
-    DKM_TRY(apply_tiling(c));
+    dkm_status r = apply_tiling(c);
+    if (r != DKM_OK) {
+      c->ready = false;   // the point index is half re-cut: a dkm_setup must rebuild it
+      return r;
+    }
     changed = true;
   }
   if (t.row_filter_min != c->row_filter_min) {
