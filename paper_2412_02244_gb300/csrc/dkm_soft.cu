@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
     } else {
       for (int j = 0; j < k; ++j) m = fminf(m, sqd<D>(p, sc[j], dv));
       float z = 0.f;
-      for (int j = 0; j < k; ++j) z += expf((m - sqd<D>(p, sc[j], dv)) * it);
+      for (int j = 0; j < k; ++j) z += __expf((m - sqd<D>(p, sc[j], dv)) * it);
       iz = 1.f / z;
     }
     if (MODE == kRowLoss || MODE == kRowLossBwd) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
       float3 Bv = make_float3(0.f, 0.f, 0.f), F = make_float3(0.f, 0.f, 0.f);
       for (int j = 0; j < k; ++j) {
         const float s = sqd<D>(p, sc[j], dv);
-        const float w = expf((m - s) * it) * iz;
+        const float w = __expf((m - s) * it) * iz;
         E = __fmaf_rn(w, s, E);
         if (MODE == kRowLossBwd) {
           Bv.x = __fmaf_rn(w, dv.x, Bv.x); Bv.y = __fmaf_rn(w, dv.y, Bv.y); Bv.z = __fmaf_rn(w, dv.z, Bv.z);
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
       float3 Av = make_float3(0.f, 0.f, 0.f), Bv = Av, Dir = Av;
       for (int j = 0; j < k; ++j) {
         const float s = sqd<D>(p, sc[j], dv);
-        const float w = expf((m - s) * it) * iz;
+        const float w = __expf((m - s) * it) * iz;
         const float4 cn = scn[j], gb = sg[j];
         float3 dn;
         sqd<D>(p, cn, dn);
@@ -266,7 +266,7 @@ __global__ void k_soft_col(SoftArgs A, const float* __restrict__ Ct, const float
           continue;
         }
         const float sd = sqd<D>(p, c, dv);
-        const float w = expf((pq.w - sd) * it) * aq.x;
+        const float w = __expf((pq.w - sd) * it) * aq.x;
         if (MODE == kColMean) {
           f[0] = __fmaf_rn(w, p.x, f[0]);
           f[1] = __fmaf_rn(w, p.y, f[1]);
