@@ -166,7 +166,7 @@ struct Layout {
 
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
-  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_counts, rs_totals, tbox, tiles, n_tiles,
+  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_scratch, tbox, tiles, n_tiles,
       tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
@@ -193,8 +193,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.keys1 = L.take<uint32_t>(n);
   P.vals0 = L.take<uint32_t>(n);
   P.vals1 = L.take<uint32_t>(n);
-  P.rs_counts = L.take<uint32_t>(256 * radix_sort_nb(n));
-  P.rs_totals = L.take<uint32_t>(256);
+  P.rs_scratch = L.take<unsigned char>(rs_scratch_bytes(n));
   P.tbox = L.take<float4>(2 * tm);
   P.tiles = L.take<int2>(tm);
   P.n_tiles = L.take<int>(1);
@@ -746,16 +745,16 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   }
   DKM_TRY(plan_clouds(c, blo, bhi));
   DKM_TRY(upload_clouds(c));
-  DKM_CK(launch_morton(src, c->n, c->d, c->doff, c->B, c->clouds, c->mb, c->keys[0], c->vals[0],
-                       c->stream));
   int fin = 0;
   // The top 24 key bits are sorted: the lower ones only order points inside
   // the finest Morton cells, far below the cube level tiles are cut at, and
   // every order is a valid index (tiles are cut wherever the compared key
   // bits change, and boxes are taken from the points themselves).
   const int bits_lo = c->key_bits > 24 ? c->key_bits - 24 : 0;
-  DKM_CK(launch_radix_sort(c->keys, c->vals, c->n, bits_lo, c->key_bits, c->rs_counts,
-                           c->rs_totals, &fin, c->stream));
+  DKM_CK(launch_morton(src, c->n, c->d, c->doff, c->B, c->clouds, c->mb, c->keys[0], bits_lo,
+                       c->key_bits, c->rs_scratch, c->stream));
+  DKM_CK(launch_radix_sort(c->keys, c->vals, c->n, bits_lo, c->key_bits, c->rs_scratch, c->st,
+                           &fin, c->stream));
   c->perm = c->vals[fin];
   c->skeys = c->keys[fin];
   DKM_CK(launch_gather(src, c->n, c->d, c->perm, c->xs, c->ys, c->zs, c->n_pad, c->stream));
@@ -764,7 +763,10 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   DKM_CK(cudaMemcpyAsync(c->h_level_hist.data(), c->level_hist,
                          sizeof(unsigned long long) * c->h_level_hist.size(),
                          cudaMemcpyDeviceToHost, c->stream));
+  DKM_CK(cudaMemcpyAsync(pin_state(c), c->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                         c->stream));
   DKM_CK(cudaStreamSynchronize(c->stream));
+  if (pin_state(c)->sort_err) return fail(DKM_EINTERNAL, "radix sort: a look-back wait timed out");
   DKM_TRY(apply_tiling(c));
   DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
   if (c->opts.profile) {   // read out lazily (dkm_last_timings), no synchronisation here
@@ -847,8 +849,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->keys[1] = (uint32_t*)(base + P.keys1);
   c->vals[0] = (uint32_t*)(base + P.vals0);
   c->vals[1] = (uint32_t*)(base + P.vals1);
-  c->rs_counts = (uint32_t*)(base + P.rs_counts);
-  c->rs_totals = (uint32_t*)(base + P.rs_totals);
+  c->rs_scratch = (void*)(base + P.rs_scratch);
   c->tbox = (float4*)(base + P.tbox);
   c->tiles = (int2*)(base + P.tiles);
   c->n_tiles_dev = (int*)(base + P.n_tiles);

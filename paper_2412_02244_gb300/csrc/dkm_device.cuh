@@ -53,7 +53,7 @@ struct DevState {
   int passes;            // max over clouds of the passes of the current run
   int err;               // internal error bits (kErr*)
   int label_err;         // dkm_update: a label outside [0, k_b)
-  int pad0;
+  int sort_err;          // dkm_setup: a radix-sort look-back gave up waiting
   unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles, last_stays;
   unsigned long long grid_ovf;   // centroids put in an overflow list, last rebuild
   double last_sse;               // total SSE of the last pass (against its input centroids)

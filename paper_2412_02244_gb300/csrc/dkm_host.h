@@ -17,11 +17,11 @@ cudaError_t launch_bbox(const float* p, int d, const int64_t* seg, int B, int64_
                         CloudRun* crun, DevState* st, int which, int d_ctx, cudaStream_t s);
 cudaError_t launch_exponents(const Cloud* clouds, CloudRun* crun, int B, cudaStream_t s);
 cudaError_t launch_morton(const float* p, int64_t n, int d, const int64_t* seg, int B,
-                          const Cloud* clouds, int mb, uint32_t* keys, uint32_t* vals,
-                          cudaStream_t s);
-int64_t radix_sort_nb(int64_t n);
+                          const Cloud* clouds, int mb, uint32_t* keys, int bits_lo, int bits_hi,
+                          void* scratch, cudaStream_t s);
+size_t rs_scratch_bytes(int64_t n);
 cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits_lo,
-                              int bits_hi, uint32_t* counts, uint32_t* totals, int* final_buf,
+                              int bits_hi, void* scratch, DevState* st, int* final_buf,
                               cudaStream_t s);
 cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,
                           float* ys, float* zs, int64_t n_pad, cudaStream_t s);
@@ -103,7 +103,7 @@ struct dkm_ctx {
   uint32_t* vals[2] = {nullptr, nullptr};
   uint32_t* skeys = nullptr;   // sorted keys (one of keys[])
   uint32_t* perm = nullptr;    // sorted position -> original index
-  uint32_t *rs_counts = nullptr, *rs_totals = nullptr;
+  void* rs_scratch = nullptr;  // radix sort: digit counts, tickets, look-back words
   float4* tbox = nullptr;
   int2* tiles = nullptr;
   int* n_tiles_dev = nullptr;

@@ -15,7 +15,8 @@
 //                  mb bits per axis on the cloud's own box (mb = 10 in 3D
 //                  and 15 in 2D for a single cloud, fewer when the cloud
 //                  index needs the top bits)
-//   k_rs_*         stable LSD radix sort of (key, index), 8-bit digits
+//   k_rs_onesweep  stable LSD radix sort of (key, index), 8-bit digits,
+//                  one kernel per digit
 //   k_gather       sorted structure-of-arrays copy of the points
 //   k_levels       per cloud, how many Morton cubes each level would cut
 //                  the order into
@@ -26,8 +27,9 @@
 namespace dkm {
 
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 8;
-constexpr int kRsTile = kRsThreads * kRsItems;   // 2048 keys per CTA
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;   // 4096 keys per CTA of the sort
+constexpr int kRsMaxPasses = 4;                  // 8-bit digits of a 32-bit key
 constexpr float kMaxAbsCoord = 1.0e18f;          // larger coordinates are rejected
 
 // ---------------------------------------------------------------------------
@@ -91,7 +93,10 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int d
 // the z range to [0, 0]) and clear the bad-input flag
 __global__ void k_reset_boxes(CloudRun* crun, int B, DevState* st, int d, int which_mask) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b == 0) st->bad = 0;
+  if (b == 0) {
+    st->bad = 0;
+    if (which_mask & 1) st->sort_err = 0;
+  }
   if (b >= B) return;
   for (int w = 0; w < 2; ++w) {
     if (!(which_mask & (1 << w))) continue;
@@ -136,55 +141,83 @@ __device__ __forceinline__ uint32_t spread2(uint32_t v) {   // 15 bits -> every 
 
 // Key of a point of cloud b: b in the bits above d * mb, then the Morton
 // code of its mb-bit-per-axis lattice coordinates on the cloud's own box.
+// The CTA also counts, for each of the npass sort passes, how many keys
+// have each 8-bit digit (key >> (shift0 + 8 q)) & 255 (hist, npass x 256,
+// zeroed beforehand).  A warp whose 32 keys share a digit adds 32 once,
+// which keeps spatially coherent input free of shared-memory contention.
 __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ p, int64_t n, int d,
                                                 const int64_t* __restrict__ seg, int B,
                                                 const Cloud* __restrict__ clouds, int mb,
-                                                uint32_t* __restrict__ keys,
-                                                uint32_t* __restrict__ vals) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int b = B > 1 ? seg_of(seg, B, i) : 0;
-  const Cloud& c = clouds[b];
+                                                uint32_t* __restrict__ keys, int shift0, int npass,
+                                                uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kRsMaxPasses][256];
+  for (int t = threadIdx.x; t < kRsMaxPasses * 256; t += blockDim.x) (&h[0][0])[t] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
   const float qmax = (float)((1u << mb) - 1u);
-  const float inv = c.minv;
-  float q0 = fminf(fmaxf((p[i * d + 0] - c.mlo[0]) * inv, 0.f), qmax);
-  float q1 = fminf(fmaxf((p[i * d + 1] - c.mlo[1]) * inv, 0.f), qmax);
-  uint32_t key;
-  if (d == 3) {
-    float q2 = fminf(fmaxf((p[i * d + 2] - c.mlo[2]) * inv, 0.f), qmax);
-    key = spread3((uint32_t)q0) | (spread3((uint32_t)q1) << 1) | (spread3((uint32_t)q2) << 2);
-  } else {
-    key = spread2((uint32_t)q0) | (spread2((uint32_t)q1) << 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the loop bound is uniform over the CTA: every lane takes part in the votes
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool v = i < n;
+    uint32_t key = 0;
+    if (v) {
+      const int b = B > 1 ? seg_of(seg, B, i) : 0;
+      const Cloud& c = clouds[b];
+      const float inv = c.minv;
+      const float q0 = fminf(fmaxf((p[i * d + 0] - c.mlo[0]) * inv, 0.f), qmax);
+      const float q1 = fminf(fmaxf((p[i * d + 1] - c.mlo[1]) * inv, 0.f), qmax);
+      if (d == 3) {
+        const float q2 = fminf(fmaxf((p[i * d + 2] - c.mlo[2]) * inv, 0.f), qmax);
+        key = spread3((uint32_t)q0) | (spread3((uint32_t)q1) << 1) | (spread3((uint32_t)q2) << 2);
+      } else {
+        key = spread2((uint32_t)q0) | (spread2((uint32_t)q1) << 1);
+      }
+      if (B > 1) key |= (uint32_t)b << (d * mb);
+      keys[i] = key;
+    }
+    for (int q = 0; q < npass; ++q) {
+      const uint32_t dig = (key >> (shift0 + 8 * q)) & 0xffu;
+      const uint32_t d0 = __shfl_sync(0xffffffffu, dig, 0);
+      if (__all_sync(0xffffffffu, v && dig == d0)) {
+        if (lane == 0) atomicAdd(&h[q][d0], 32u);
+      } else if (v) {
+        atomicAdd(&h[q][dig], 1u);
+      }
+    }
   }
-  if (B > 1) key |= (uint32_t)b << (d * mb);
-  keys[i] = key;
-  vals[i] = (uint32_t)i;
+  __syncthreads();
+  for (int t = threadIdx.x; t < npass * 256; t += blockDim.x) {
+    const uint32_t c = (&h[0][0])[t];
+    if (c) atomicAdd(&hist[t], c);
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits.  Per pass: upsweep (per-CTA digit
-// counts, digit-major), scan (one CTA per digit), downsweep (stable rank via
-// warp match + per-warp counters, then scatter).
+// Stable LSD radix sort of (key, index) pairs, 8-bit digits, one kernel per
+// digit (single-pass "onesweep" scheme).  k_morton has already counted every
+// digit of every pass over the whole array; each CTA of k_rs_onesweep takes
+// the next 4096-key tile in input order (a ticket, so every lower tile is
+// already running), ranks its keys stably, publishes its per-digit counts,
+// sums the counts of the lower tiles by decoupled look-back, and scatters.
+//
+// Look-back words, one per (tile, digit): tag in the high 32 bits (2p + 1:
+// the tile's own count for pass p, 2p + 2: the inclusive prefix up to and
+// including the tile), the count in the low 32 bits.  The buffer is zeroed
+// once per sort; a word left by an earlier pass carries an older tag and
+// reads as "not yet published".  Every wait is bounded: a look-back that
+// polls kRsSpinLimit times sets DevState.sort_err and stops.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const uint32_t* __restrict__ keys,
-                                                           int64_t n, int shift,
-                                                           uint32_t* __restrict__ counts, int nb) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * kRsTile;
-  int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < kRsItems; ++j) {
-    int64_t i = base + (int64_t)j * kRsThreads + threadIdx.x;
-    bool v = i < n;
-    uint32_t dig = v ? ((keys[i] >> shift) & 0xffu) : 0x100u;
-    uint32_t peers = __match_any_sync(0xffffffffu, dig);
-    int leader = __ffs(peers) - 1;
-    if (v && lane == leader) atomicAdd(&h[dig], (uint32_t)__popc(peers));
-  }
-  __syncthreads();
-  counts[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+constexpr int kRsSpinLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // exclusive scan of one value per thread across a 256-thread CTA
@@ -214,86 +247,95 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t v, uint32_t
   return before + x - v;
 }
 
-__global__ void __launch_bounds__(256) k_rs_scan(uint32_t* __restrict__ counts, int nb,
-                                                 uint32_t* __restrict__ totals) {
-  __shared__ uint32_t s_warp[16];
-  uint32_t* row = counts + (int64_t)blockIdx.x * nb;
-  int per = (nb + 255) / 256;
-  int start = threadIdx.x * per;
-  uint32_t sum = 0;
-  for (int i = start; i < start + per && i < nb; ++i) sum += row[i];
-  uint32_t tot;
-  uint32_t run = block_exclusive_scan256(sum, s_warp, &tot);
-  for (int i = start; i < start + per && i < nb; ++i) {
-    uint32_t c = row[i];
-    row[i] = run;
-    run += c;
-  }
-  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
-}
-
-// The CTA's keys are first placed in shared memory grouped by digit (stable:
-// warp, then item, then lane order), then written out digit run by digit
-// run, so consecutive threads store to consecutive addresses.
-__global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
+// One pass: digit (key >> shift) & 255 of pass `pass`.  vin == nullptr
+// stands for the identity (vals[i] = i) on the first pass.  The CTA's keys
+// are ranked per warp (warp match + per-warp counters: stable in warp,
+// item, lane order, which is the input order), placed in shared memory
+// grouped by digit, then written out digit run by digit run so that
+// consecutive threads store to consecutive addresses.
+__global__ void __launch_bounds__(kRsThreads, 3) k_rs_onesweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ counts,
-    const uint32_t* __restrict__ totals, int nb) {
+    uint32_t* __restrict__ vout, int64_t n, int shift, int pass,
+    const uint32_t* __restrict__ hist, unsigned long long* status, uint32_t* ticket,
+    DevState* st) {
   __shared__ uint32_t whist[8][256];
   __shared__ uint32_t goff[256];
   __shared__ uint32_t lbase[256];
   __shared__ uint32_t s_warp[16];
   __shared__ uint32_t skey[kRsTile];
   __shared__ uint32_t sval[kRsTile];
+  __shared__ int s_tile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket + pass, 1u);
   for (int t = threadIdx.x; t < 8 * 256; t += kRsThreads) (&whist[0][0])[t] = 0;
-  uint32_t tot = totals[threadIdx.x];
-  uint32_t digit_base = block_exclusive_scan256(tot, s_warp, nullptr);
-  goff[threadIdx.x] = digit_base + counts[(int64_t)threadIdx.x * nb + blockIdx.x];
   __syncthreads();
-
-  const int64_t cta0 = (int64_t)blockIdx.x * kRsTile;
+  const int tile = s_tile;
+  const int64_t cta0 = (int64_t)tile * kRsTile;
   const int64_t base = cta0 + (int64_t)w * (32 * kRsItems);
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t key[kRsItems], val[kRsItems], rank[kRsItems];
 #pragma unroll
   for (int j = 0; j < kRsItems; ++j) {
-    int64_t i = base + j * 32 + lane;
-    bool v = i < n;
+    const int64_t i = base + j * 32 + lane;
+    const bool v = i < n;
     key[j] = v ? kin[i] : 0u;
-    val[j] = v ? vin[i] : 0u;
+    val[j] = v ? (vin ? vin[i] : (uint32_t)i) : 0u;
   }
 #pragma unroll
   for (int j = 0; j < kRsItems; ++j) {
-    int64_t i = base + j * 32 + lane;
-    bool v = i < n;
-    uint32_t dig = v ? ((key[j] >> shift) & 0xffu) : 0x100u;
-    uint32_t peers = __match_any_sync(0xffffffffu, dig);
-    int leader = 31 - __clz(peers);
-    uint32_t b = v ? whist[w][dig] : 0u;
+    const int64_t i = base + j * 32 + lane;
+    const bool v = i < n;
+    const uint32_t dig = v ? ((key[j] >> shift) & 0xffu) : 0x100u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+    const int leader = 31 - __clz(peers);
+    const uint32_t b = v ? whist[w][dig] : 0u;
     __syncwarp();
     if (v && lane == leader) whist[w][dig] = b + (uint32_t)__popc(peers);
     __syncwarp();
     rank[j] = b + (uint32_t)__popc(peers & lt);
   }
   __syncthreads();
+  const int d = threadIdx.x;   // this thread's digit from here on
   uint32_t run = 0;
-  {   // per digit: exclusive prefix over warps (warp order = input order)
-    for (int ww = 0; ww < 8; ++ww) {
-      uint32_t c = whist[ww][threadIdx.x];
-      whist[ww][threadIdx.x] = run;
-      run += c;
-    }
+  for (int ww = 0; ww < 8; ++ww) {   // per digit: exclusive prefix over warps
+    const uint32_t c = whist[ww][d];
+    whist[ww][d] = run;
+    run += c;
   }
-  // start of each digit's run inside this CTA's block of keys
-  lbase[threadIdx.x] = block_exclusive_scan256(run, s_warp, nullptr);
+  const unsigned long long tag_own = 2ull * pass + 1ull, tag_incl = 2ull * pass + 2ull;
+  unsigned long long* my = status + (int64_t)tile * 256 + d;
+  st_relaxed_u64(my, ((tile == 0 ? tag_incl : tag_own) << 32) | run);
+  lbase[d] = block_exclusive_scan256(run, s_warp, nullptr);
+  const uint32_t dstart = block_exclusive_scan256(hist[pass * 256 + d], s_warp, nullptr);
+  uint32_t excl = 0;
+  if (tile > 0) {
+    int64_t tt = tile - 1;
+    int polls = 0;
+    while (tt >= 0) {
+      const unsigned long long v = ld_relaxed_u64(status + tt * 256 + d);
+      const unsigned long long tag = v >> 32;
+      if (tag == tag_incl || tag == tag_own) {
+        excl += (uint32_t)v;
+        if (tag == tag_incl) break;
+        --tt;
+        continue;
+      }
+      if (++polls > kRsSpinLimit) {
+        atomicOr(&st->sort_err, 1);
+        break;
+      }
+      if (polls > 8) __nanosleep(64);
+    }
+    st_relaxed_u64(my, (tag_incl << 32) | (excl + run));
+  }
+  goff[d] = dstart + excl;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kRsItems; ++j) {
-    int64_t i = base + j * 32 + lane;
+    const int64_t i = base + j * 32 + lane;
     if (i < n) {
-      uint32_t dig = (key[j] >> shift) & 0xffu;
-      uint32_t loc = lbase[dig] + whist[w][dig] + rank[j];
+      const uint32_t dig = (key[j] >> shift) & 0xffu;
+      const uint32_t loc = lbase[dig] + whist[w][dig] + rank[j];
       skey[loc] = key[j];
       sval[loc] = val[j];
     }
@@ -304,8 +346,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
     const uint32_t k = skey[i];
     const uint32_t dig = (k >> shift) & 0xffu;
     const uint32_t pos = goff[dig] + ((uint32_t)i - lbase[dig]);
-    kout[pos] = k;
-    vout[pos] = sval[i];
+    if ((int64_t)pos < n) {   // always, unless a look-back gave up (sort_err)
+      kout[pos] = k;
+      vout[pos] = sval[i];
+    }
   }
 }
 
@@ -507,25 +551,46 @@ cudaError_t launch_exponents(const Cloud* clouds, CloudRun* crun, int B, cudaStr
   return cudaGetLastError();
 }
 
+// Scratch of the sort (rs_scratch_bytes): npass x 256 digit counts, the
+// passes' tickets, then one look-back word per (tile, digit).
+constexpr size_t kRsHistWords = kRsMaxPasses * 256 + 64;
+
+size_t rs_scratch_bytes(int64_t n) {
+  return kRsHistWords * sizeof(uint32_t) +
+         (size_t)((n + kRsTile - 1) / kRsTile) * 256 * sizeof(unsigned long long);
+}
+
+int rs_passes(int bits_lo, int bits_hi) { return (bits_hi - bits_lo + 7) / 8; }
+
 cudaError_t launch_morton(const float* p, int64_t n, int d, const int64_t* seg, int B,
-                          const Cloud* clouds, int mb, uint32_t* keys, uint32_t* vals,
-                          cudaStream_t s) {
-  k_morton<<<grid_for(n, 256, 1 << 30), 256, 0, s>>>(p, n, d, seg, B, clouds, mb, keys, vals);
+                          const Cloud* clouds, int mb, uint32_t* keys, int bits_lo, int bits_hi,
+                          void* scratch, cudaStream_t s) {
+  const int npass = rs_passes(bits_lo, bits_hi);
+  if (npass < 1 || npass > kRsMaxPasses) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, rs_scratch_bytes(n), s);
+  if (e != cudaSuccess) return e;
+  k_morton<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(p, n, d, seg, B, clouds, mb, keys, bits_lo,
+                                                     npass, (uint32_t*)scratch);
   return cudaGetLastError();
 }
 
-int64_t radix_sort_nb(int64_t n) { return (n + kRsTile - 1) / kRsTile; }
-
+// Sorts keys[0] (and the identity permutation) on bits [bits_lo, bits_hi);
+// *final_buf: the buffer pair holding the result.  Expects launch_morton's
+// digit counts and zeroed look-back words in scratch.
 cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits_lo,
-                              int bits_hi, uint32_t* counts, uint32_t* totals, int* final_buf,
+                              int bits_hi, void* scratch, DevState* st, int* final_buf,
                               cudaStream_t s) {
-  int nb = (int)radix_sort_nb(n);
+  const int npass = rs_passes(bits_lo, bits_hi);
+  if (npass < 1 || npass > kRsMaxPasses) return cudaErrorInvalidValue;
+  uint32_t* hist = (uint32_t*)scratch;
+  uint32_t* ticket = hist + kRsMaxPasses * 256;
+  unsigned long long* status = (unsigned long long*)(hist + kRsHistWords);
+  const int nt = (int)((n + kRsTile - 1) / kRsTile);
   int cur = 0;
-  for (int shift = bits_lo; shift < bits_hi; shift += 8) {
-    k_rs_upsweep<<<nb, kRsThreads, 0, s>>>(keys[cur], n, shift, counts, nb);
-    k_rs_scan<<<256, 256, 0, s>>>(counts, nb, totals);
-    k_rs_downsweep<<<nb, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1],
-                                             n, shift, counts, totals, nb);
+  for (int q = 0; q < npass; ++q) {
+    k_rs_onesweep<<<nt, kRsThreads, 0, s>>>(keys[cur], q == 0 ? nullptr : vals[cur],
+                                            keys[cur ^ 1], vals[cur ^ 1], n, bits_lo + 8 * q, q,
+                                            hist, status, ticket, st);
     cur ^= 1;
   }
   *final_buf = cur;
