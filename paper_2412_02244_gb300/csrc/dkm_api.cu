@@ -166,8 +166,8 @@ struct Layout {
 
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
-  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_scratch, tbox, tiles, n_tiles,
-      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, wcnt, wbase, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+  size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_scratch, tbox, tiles,
+      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, tl_scan, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
 };
@@ -196,7 +196,6 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.rs_scratch = L.take<unsigned char>(rs_scratch_bytes(n));
   P.tbox = L.take<float4>(2 * tm);
   P.tiles = L.take<int2>(tm);
-  P.n_tiles = L.take<int>(1);
   P.tcloud = L.take<int>(tm);
   P.tfirst = L.take<int>(B);
   P.kcloud = L.take<int>(k);
@@ -206,8 +205,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.tunit = L.take<int>(tm);
   P.cb2 = L.take<float>(k);
   P.tlab = L.take<int>(tm);
-  P.wcnt = L.take<int>(nw);
-  P.wbase = L.take<int>(nw);
+  P.tl_scan = L.take<unsigned long long>(tiles_scan_words((int)nw));
   P.level_hist = L.take<unsigned long long>(B * (kMaxLevels + 1));
   P.doff = L.take<int64_t>(B + 1);
   P.dcoff = L.take<int64_t>(B + 1);
@@ -634,39 +632,37 @@ dkm_status plan_clouds(dkm_ctx* c, const std::vector<float>& blo, const std::vec
 
 dkm_status apply_units(dkm_ctx* c);
 
-// Tiles from the level histogram: per cloud the finest Morton level whose
-// cubes cut its sorted run into at most max(1, windows_b / cut_div) pieces
-// (so cube cuts add few tiles), then tile ranges, boxes and the tile ->
-// cloud map.
-dkm_status apply_tiling(dkm_ctx* c) {
-  const int L = c->mb;
-  for (int b = 0; b < c->B; ++b) {
-    const unsigned long long* h = &c->h_level_hist[(size_t)b * (kMaxLevels + 1)];
-    const int64_t nw_b = windows_of(c->h_clouds[b].n);
-    const unsigned long long seg_cap =
-        (unsigned long long)std::max<int64_t>(1, nw_b / c->cut_div);
-    int level = 0;
-    unsigned long long segs = 1;
-    for (int l = 1; l <= L; ++l) {
-      segs += h[l];
-      if (segs > seg_cap) break;
-      level = l;
-    }
-    c->h_clouds[b].shift = c->d * (L - level);
-    if (b == 0) c->tile_level = level;
-  }
-  DKM_TRY(upload_clouds(c));
-  DKM_CK(launch_tiles(c->skeys, c->n, c->clouds, c->d, c->mb, c->B, c->n_windows, c->wcnt,
-                      c->wbase, c->n_tiles_dev, c->tiles, c->stream));
-  int nt = 0;
-  DKM_CK(cudaMemcpyAsync(&nt, c->n_tiles_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  DKM_CK(cudaStreamSynchronize(c->stream));
+// Tiles from the level histogram (device work only, no synchronisation):
+// per cloud the cube level the tiles are cut at (k_choose_levels), then tile
+// ranges, boxes, the tile -> cloud map and the tile count (DevState.tiles).
+dkm_status launch_tiling(dkm_ctx* c) {
+  DKM_CK(launch_tiles(c->skeys, c->n, c->clouds, c->d, c->mb, c->B, c->cut_div, c->level_hist,
+                      c->n_windows, c->xs, c->ys, c->zs, c->tl_scan, c->tiles_cap, c->tiles,
+                      c->tbox, c->tcloud, c->tfirst, &c->st->tiles, c->st, c->stream));
+  return DKM_OK;
+}
+
+// Host side of a tiling, from the synchronised DevState and cloud table
+// (pinned copies): the cut shifts and the tile count.
+dkm_status finish_tiling(dkm_ctx* c, const DevState& h, const Cloud* dev_clouds) {
+  if (h.sort_err) return fail(DKM_EINTERNAL, "index build: a look-back wait timed out");
+  for (int b = 0; b < c->B; ++b) c->h_clouds[b].shift = dev_clouds[b].shift;
+  c->tile_level = c->mb - c->h_clouds[0].shift / c->d;
+  const int nt = h.tiles;
   if (nt < 1 || nt > c->tiles_cap) return fail(DKM_EINTERNAL, "tile count %d out of range", nt);
   c->n_tiles = nt;
-  // candidate lists of the old tiles must not seed the new ones
-  DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
-  DKM_CK(launch_tile_boxes(c->xs, c->ys, c->zs, c->d, c->tiles, nt, c->skeys, c->mb, c->B,
-                           c->tbox, c->tcloud, c->tfirst, c->stream));
+  return DKM_OK;
+}
+
+// Re-cut the tiles of the current point index (a new tile_cut_div).
+dkm_status apply_tiling(dkm_ctx* c) {
+  DKM_TRY(launch_tiling(c));
+  DKM_CK(cudaMemcpyAsync(pin_state(c), c->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                         c->stream));
+  DKM_CK(cudaMemcpyAsync(pin_clouds(c), c->clouds, sizeof(Cloud) * c->B, cudaMemcpyDeviceToHost,
+                         c->stream));
+  DKM_CK(cudaStreamSynchronize(c->stream));
+  DKM_TRY(finish_tiling(c, *pin_state(c), pin_clouds(c)));
   return apply_units(c);
 }
 
@@ -727,24 +723,16 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
     src = c->pstage;
   }
   if (c->opts.profile) DKM_CK(cudaEventRecord(c->ev_s0, c->stream));
-  DKM_CK(launch_bbox(src, c->d, c->doff, c->B, c->max_n_b, c->crun, c->st, 0, c->d, c->stream));
-  DevState h;
-  std::vector<CloudRun> hr;
-  DKM_TRY(read_state_clouds(c, &h, &hr));
-  if (h.bad) return fail(DKM_EINVAL, "points contain a non-finite or |x| > 1e18 coordinate");
-  cloud_boxes(c, hr, &c->h_blo, &c->h_bhi);
-  const std::vector<float>& blo = c->h_blo;
-  const std::vector<float>& bhi = c->h_bhi;
-  // Morton lattice of each cloud: a cube of (2^mb - 1) steps over its box
-  const float qmax = (float)((1u << c->mb) - 1u);
-  for (int b = 0; b < c->B; ++b) {
-    float emax = 0.f;
-    for (int a = 0; a < c->d; ++a) emax = std::max(emax, bhi[3 * b + a] - blo[3 * b + a]);
-    for (int a = 0; a < 3; ++a) c->h_clouds[b].mlo[a] = blo[3 * b + a];
-    c->h_clouds[b].minv = emax > 0.f ? qmax / emax : 0.f;
-  }
-  DKM_TRY(plan_clouds(c, blo, bhi));
+  // Everything up to the tiles runs on the device without a host round
+  // trip (the Morton lattice and the cut levels are computed there); one
+  // synchronisation at the end brings back the boxes, the cloud table, the
+  // tile count and the error flags.  Non-finite input is rejected then: the
+  // kernels before clamp every key into range, so they stay in bounds.
+  // the device cloud table must hold every cloud's point range before the
+  // lattice and level kernels fill in their fields
   DKM_TRY(upload_clouds(c));
+  DKM_CK(launch_bbox(src, c->d, c->doff, c->B, c->max_n_b, c->crun, c->st, 0, c->d, c->stream));
+  DKM_CK(launch_lattice(c->clouds, c->crun, c->B, c->d, c->mb, c->stream));
   int fin = 0;
   // The top 24 key bits are sorted: the lower ones only order points inside
   // the finest Morton cells, far below the cube level tiles are cut at, and
@@ -759,16 +747,24 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   c->skeys = c->keys[fin];
   DKM_CK(launch_gather(src, c->n, c->d, c->perm, c->xs, c->ys, c->zs, c->n_pad, c->stream));
   DKM_CK(launch_levels(c->skeys, c->n, c->d, c->mb, c->B, c->level_hist, c->stream));
-  c->h_level_hist.assign((size_t)c->B * (kMaxLevels + 1), 0ull);
-  DKM_CK(cudaMemcpyAsync(c->h_level_hist.data(), c->level_hist,
-                         sizeof(unsigned long long) * c->h_level_hist.size(),
-                         cudaMemcpyDeviceToHost, c->stream));
-  DKM_CK(cudaMemcpyAsync(pin_state(c), c->st, sizeof(DevState), cudaMemcpyDeviceToHost,
-                         c->stream));
-  DKM_CK(cudaStreamSynchronize(c->stream));
-  if (pin_state(c)->sort_err) return fail(DKM_EINTERNAL, "radix sort: a look-back wait timed out");
-  DKM_TRY(apply_tiling(c));
+  DKM_TRY(launch_tiling(c));
   DKM_CK(cudaMemsetAsync(c->lab, 0xff, (size_t)c->n_pad * sizeof(int32_t), c->stream));
+  DKM_CK(cudaMemcpyAsync(pin_clouds(c), c->clouds, sizeof(Cloud) * c->B, cudaMemcpyDeviceToHost,
+                         c->stream));
+  DevState h;
+  std::vector<CloudRun> hr;
+  DKM_TRY(read_state_clouds(c, &h, &hr));
+  if (h.bad) return fail(DKM_EINVAL, "points contain a non-finite or |x| > 1e18 coordinate");
+  cloud_boxes(c, hr, &c->h_blo, &c->h_bhi);
+  for (int b = 0; b < c->B; ++b) {
+    const Cloud& dc = pin_clouds(c)[b];
+    for (int a = 0; a < 3; ++a) c->h_clouds[b].mlo[a] = dc.mlo[a];
+    c->h_clouds[b].minv = dc.minv;
+  }
+  DKM_TRY(finish_tiling(c, h, pin_clouds(c)));
+  DKM_TRY(plan_clouds(c, c->h_blo, c->h_bhi));
+  DKM_TRY(upload_clouds(c));
+  DKM_TRY(apply_units(c));
   if (c->opts.profile) {   // read out lazily (dkm_last_timings), no synchronisation here
     DKM_CK(cudaEventRecord(c->ev_s, c->stream));
     c->setup_pending = true;
@@ -852,7 +848,6 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->rs_scratch = (void*)(base + P.rs_scratch);
   c->tbox = (float4*)(base + P.tbox);
   c->tiles = (int2*)(base + P.tiles);
-  c->n_tiles_dev = (int*)(base + P.n_tiles);
   c->tcloud = (int*)(base + P.tcloud);
   c->tfirst = (int*)(base + P.tfirst);
   c->kcloud = (int*)(base + P.kcloud);
@@ -862,8 +857,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->tunit = (int*)(base + P.tunit);
   c->cb2 = (float*)(base + P.cb2);
   c->tlab = (int*)(base + P.tlab);
-  c->wcnt = (int*)(base + P.wcnt);
-  c->wbase = (int*)(base + P.wbase);
+  c->tl_scan = (unsigned long long*)(base + P.tl_scan);
   c->level_hist = (unsigned long long*)(base + P.level_hist);
   c->doff = (int64_t*)(base + P.doff);
   c->dcoff = (int64_t*)(base + P.dcoff);

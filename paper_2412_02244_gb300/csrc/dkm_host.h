@@ -27,12 +27,14 @@ cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* orde
                           float* ys, float* zs, int64_t n_pad, cudaStream_t s);
 cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,
                           unsigned long long* hist, cudaStream_t s);
-cudaError_t launch_tiles(const uint32_t* keys, int64_t n, const Cloud* clouds, int d, int mb,
-                         int B, int n_windows, int* wcnt, int* wbase, int* n_tiles, int2* tiles,
-                         cudaStream_t s);
-cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
-                              const int2* tiles, int n_tiles, const uint32_t* keys, int mb, int B,
-                              float4* tbox, int* tcloud, int* tfirst, cudaStream_t s);
+cudaError_t launch_lattice(Cloud* clouds, const CloudRun* crun, int B, int d, int mb,
+                           cudaStream_t s);
+size_t tiles_scan_words(int n_windows);
+cudaError_t launch_tiles(const uint32_t* keys, int64_t n, Cloud* clouds, int d, int mb, int B,
+                         int cut_div, const unsigned long long* level_hist, int n_windows,
+                         const float* xs, const float* ys, const float* zs,
+                         unsigned long long* scan, int tiles_cap, int2* tiles, float4* tbox,
+                         int* tcloud, int* tfirst, int* n_tiles, DevState* st, cudaStream_t s);
 
 // dkm_iter.cu
 cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s);
@@ -87,7 +89,6 @@ struct dkm_ctx {
   int64_t total_cells = 0;     // cells of the current grids
   dkm_plan_info plan{};
   std::vector<dkm::Cloud> h_clouds;               // host copy of the cloud table
-  std::vector<unsigned long long> h_level_hist;   // B x (kMaxLevels + 1)
   std::vector<float> h_blo, h_bhi;                // per-cloud point boxes (3 floats each)
   int row_filter_min = 48;     // per-row candidate filtering threshold
   int sort_max = 0;            // sorted early-exit evaluation for lists up to this length
@@ -106,7 +107,6 @@ struct dkm_ctx {
   void* rs_scratch = nullptr;  // radix sort: digit counts, tickets, look-back words
   float4* tbox = nullptr;
   int2* tiles = nullptr;
-  int* n_tiles_dev = nullptr;
   int* tcloud = nullptr;
   int* tfirst = nullptr;       // per cloud: its first tile
   int* kcloud = nullptr;
@@ -114,7 +114,7 @@ struct dkm_ctx {
   int* tlab = nullptr;         // per tile: single label of its last pass, or -1
   float4* ubox = nullptr;      // per unit box (unit_g > 1)
   int *ucloud = nullptr, *ufirst = nullptr, *tunit = nullptr;
-  int *wcnt = nullptr, *wbase = nullptr;
+  unsigned long long* tl_scan = nullptr;   // k_tiles: ticket and look-back words
   unsigned long long* level_hist = nullptr;
   int64_t *doff = nullptr, *dcoff = nullptr;
   dkm::Cloud* clouds = nullptr;

@@ -20,8 +20,9 @@
 //   k_gather       sorted structure-of-arrays copy of the points
 //   k_levels       per cloud, how many Morton cubes each level would cut
 //                  the order into
-//   k_tiles_*      tiles: 256-point windows split at cube boundaries
-//   k_tile_boxes   per-tile AABBs
+//   k_choose_levels  per cloud, the cube level the tiles are cut at
+//   k_tiles        tiles (256-point windows split at cube boundaries) and
+//                  their AABBs
 #include "dkm_host.h"
 
 namespace dkm {
@@ -374,8 +375,9 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ p, int
 // cubes; a cube's points are contiguous in the sorted order.  k_levels
 // counts, per cloud and level, how many sorted neighbours first differ at
 // that level (a cube boundary of that level and every finer one); level 0
-// is a cloud boundary.  The host then picks, per cloud, the finest level
-// whose cube count keeps the cloud's extra tiles within a set fraction.
+// is a cloud boundary.  k_choose_levels then picks, per cloud, the finest
+// level whose cube count keeps the cloud's extra tiles within a set
+// fraction.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int first_diff_level(uint32_t a, uint32_t b, int d, int mb) {
   const uint32_t x = a ^ b;
@@ -426,106 +428,147 @@ __device__ __forceinline__ bool tile_starts(const uint32_t* __restrict__ keys, i
   return (k1 >> shift) != (keys[i - 1] >> shift);
 }
 
-// one warp per 256-window: number of tiles that start in it
-__global__ void __launch_bounds__(256) k_tiles_count(const uint32_t* __restrict__ keys, int64_t n,
-                                                     const Cloud* __restrict__ clouds, int d,
-                                                     int mb, int B, int n_windows,
-                                                     int* __restrict__ wcnt) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (w >= n_windows) return;
-  int c = 0;
-  for (int j = 0; j < kTilePts / 32; ++j) {
-    const int64_t i = w * kTilePts + j * 32 + lane;
-    c += __popc(__ballot_sync(0xffffffffu, i < n && tile_starts(keys, i, clouds, d, mb, B)));
+// Morton lattice of each cloud from its point box (k_bbox): a cube of
+// 2^mb - 1 steps per axis over the box's longest side.
+__global__ void k_lattice(Cloud* __restrict__ clouds, const CloudRun* __restrict__ crun, int B,
+                          int d, int mb) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float qmax = (float)((1u << mb) - 1u);
+  float emax = 0.f;
+  for (int a = 0; a < 3; ++a) {
+    const float lo = a < d ? float_of(crun[b].pbox[a]) : 0.f;
+    const float hi = a < d ? float_of(crun[b].pbox[3 + a]) : 0.f;
+    if (a < d) emax = fmaxf(emax, hi - lo);
+    clouds[b].mlo[a] = lo;
   }
-  if (lane == 0) wcnt[w] = c;
+  clouds[b].minv = emax > 0.f ? qmax / emax : 0.f;
 }
 
-// single CTA: exclusive scan of the per-window tile counts; total -> *n_tiles
-__global__ void __launch_bounds__(1024) k_scan_windows(const int* __restrict__ wcnt, int n_windows,
-                                                       int* __restrict__ wbase,
-                                                       int* __restrict__ n_tiles) {
-  __shared__ int s_part[1024];
-  const int per = (n_windows + 1023) / 1024;
-  const int start = threadIdx.x * per;
-  int sum = 0;
-  for (int i = start; i < start + per && i < n_windows; ++i) sum += wcnt[i];
-  s_part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan
-    int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
-    __syncthreads();
-    s_part[threadIdx.x] += v;
-    __syncthreads();
+// Per cloud the finest Morton level whose cubes cut its sorted run into at
+// most max(1, windows_b / cut_div) pieces, so that cube cuts add few tiles;
+// the tiles of cloud b are cut where keys differ above bit shift.
+__global__ void k_choose_levels(const unsigned long long* __restrict__ hist,
+                                Cloud* __restrict__ clouds, int B, int d, int mb, int cut_div) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const long long nw_b = (clouds[b].n + kTilePts - 1) / kTilePts;
+  const unsigned long long seg_cap = (unsigned long long)max(1ll, nw_b / cut_div);
+  const unsigned long long* h = hist + (size_t)b * (kMaxLevels + 1);
+  int level = 0;
+  unsigned long long segs = 1;
+  for (int l = 1; l <= mb; ++l) {
+    segs += h[l];
+    if (segs > seg_cap) break;
+    level = l;
   }
-  int run = s_part[threadIdx.x] - sum;
-  for (int i = start; i < start + per && i < n_windows; ++i) {
-    wbase[i] = run;
-    run += wcnt[i];
-  }
-  if (threadIdx.x == 1023) *n_tiles = s_part[1023];
+  clouds[b].shift = d * (mb - level);
 }
 
-// one warp per window: write [start, end) of every tile that starts in it
-__global__ void __launch_bounds__(256) k_tiles_write(const uint32_t* __restrict__ keys, int64_t n,
-                                                     const Cloud* __restrict__ clouds, int d,
-                                                     int mb, int B, int n_windows,
-                                                     const int* __restrict__ wbase,
-                                                     int2* __restrict__ tiles) {
+// Tiles, in one kernel.  A CTA (ticket order) takes 8 consecutive
+// 256-windows, one per warp; every window start and every cut position
+// (tile_starts) opens a tile, so a tile never leaves its window.  The CTA
+// counts its tiles, finds the number of tiles before it by decoupled
+// look-back over the lower CTAs (the radix sort's word format, tag 1: own
+// count, tag 2: inclusive prefix; bounded waits set DevState.sort_err bit
+// 2), then each warp writes its tiles' ranges, AABBs (exact min / max of
+// their points), cloud, and each cloud's first tile.  scan[0] holds the
+// ticket and scan[1 + c] CTA c's word; all zeroed beforehand.
+__global__ void __launch_bounds__(256) k_tiles(
+    const uint32_t* __restrict__ keys, int64_t n, const Cloud* __restrict__ clouds, int d, int mb,
+    int B, int n_windows, const float* __restrict__ xs, const float* __restrict__ ys,
+    const float* __restrict__ zs, unsigned long long* scan, int tiles_cap,
+    int2* __restrict__ tiles, float4* __restrict__ tbox, int* __restrict__ tcloud,
+    int* __restrict__ tfirst, int* __restrict__ n_tiles, DevState* st) {
   __shared__ int s_pos[8][kTilePts + 1];
+  __shared__ int s_cnt[8];
+  __shared__ int s_cta, s_base;
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * 8 + wl;
-  if (w >= n_windows) return;
+  if (threadIdx.x == 0) s_cta = (int)atomicAdd((unsigned*)scan, 1u);
+  __syncthreads();
+  const int cta = s_cta;
+  const int64_t w = (int64_t)cta * 8 + wl;
   const unsigned lt = (1u << lane) - 1u;
   int c = 0;
-  for (int j = 0; j < kTilePts / 32; ++j) {
-    const int64_t i = w * kTilePts + j * 32 + lane;
-    const bool f = i < n && tile_starts(keys, i, clouds, d, mb, B);
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (f) s_pos[wl][c + __popc(bal & lt)] = (int)i;
-    c += __popc(bal);
-  }
-  const int64_t wend = min((int64_t)(w + 1) * kTilePts, n);
-  if (lane == 0) s_pos[wl][c] = (int)wend;
-  __syncwarp();
-  const int base = wbase[w];
-  for (int j = lane; j < c; j += 32) tiles[base + j] = make_int2(s_pos[wl][j], s_pos[wl][j + 1]);
-}
-
-// one warp per tile: AABB of its points, its cloud, and each cloud's first
-// tile (a tile never spans two clouds)
-__global__ void __launch_bounds__(256) k_tile_boxes(const float* __restrict__ xs,
-                                                    const float* __restrict__ ys,
-                                                    const float* __restrict__ zs, int d,
-                                                    const int2* __restrict__ tiles, int n_tiles,
-                                                    const uint32_t* __restrict__ keys, int mb,
-                                                    int B, float4* __restrict__ tbox,
-                                                    int* __restrict__ tcloud,
-                                                    int* __restrict__ tfirst) {
-  const int lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (t >= n_tiles) return;
-  const int2 se = tiles[t];
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int i = se.x + lane; i < se.y; i += 32) {
-    float v0 = xs[i], v1 = ys[i], v2 = d == 3 ? zs[i] : 0.f;
-    lo[0] = fminf(lo[0], v0); hi[0] = fmaxf(hi[0], v0);
-    lo[1] = fminf(lo[1], v1); hi[1] = fmaxf(hi[1], v1);
-    lo[2] = fminf(lo[2], v2); hi[2] = fmaxf(hi[2], v2);
-  }
-  for (int a = 0; a < 3; ++a) {
-    for (int o = 16; o > 0; o >>= 1) {
-      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+  if (w < n_windows) {   // warp-uniform
+    for (int j = 0; j < kTilePts / 32; ++j) {
+      const int64_t i = w * kTilePts + j * 32 + lane;
+      const bool f = i < n && tile_starts(keys, i, clouds, d, mb, B);
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) s_pos[wl][c + __popc(bal & lt)] = (int)i;
+      c += __popc(bal);
     }
+    if (lane == 0) s_pos[wl][c] = (int)min((int64_t)(w + 1) * kTilePts, n);
   }
-  if (lane == 0) {
-    tbox[2 * t] = make_float4(lo[0], lo[1], lo[2], 0.f);
-    tbox[2 * t + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
-    const int b = cloud_of_key(keys[se.x], d, mb, B);
-    tcloud[t] = b;
-    if (se.x == 0 || cloud_of_key(keys[se.x - 1], d, mb, B) != b) tfirst[b] = t;
+  if (lane == 0) s_cnt[wl] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int q = 0; q < 8; ++q) tot += (unsigned)s_cnt[q];
+    unsigned long long* my = scan + 1 + cta;
+    st_relaxed_u64(my, ((cta == 0 ? 2ull : 1ull) << 32) | tot);
+    unsigned excl = 0;
+    if (cta > 0) {
+      int64_t q = cta - 1;
+      int polls = 0;
+      while (q >= 0) {
+        const unsigned long long v = ld_relaxed_u64(scan + 1 + q);
+        const unsigned long long tag = v >> 32;
+        if (tag == 1ull || tag == 2ull) {
+          excl += (unsigned)v;
+          if (tag == 2ull) break;
+          --q;
+          continue;
+        }
+        if (++polls > kRsSpinLimit) {
+          atomicOr(&st->sort_err, 2);
+          break;
+        }
+        if (polls > 8) __nanosleep(64);
+      }
+      st_relaxed_u64(my, (2ull << 32) | (excl + tot));
+    }
+    s_base = (int)excl;
+    if (cta == (int)gridDim.x - 1) *n_tiles = (int)(excl + tot);
+  }
+  __syncthreads();
+  if (w >= n_windows) return;
+  int base = s_base;
+  for (int q = 0; q < wl; ++q) base += s_cnt[q];
+  constexpr int kPer = kTilePts / 32;
+  float x[kPer], y[kPer], z[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {   // padded arrays: the whole window is addressable
+    const int64_t i = w * kTilePts + q * 32 + lane;
+    x[q] = xs[i];
+    y[q] = ys[i];
+    z[q] = d == 3 ? zs[i] : 0.f;
+  }
+  for (int j = 0; j < c; ++j) {
+    const int s0 = s_pos[wl][j], e0 = s_pos[wl][j + 1];
+    unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int64_t i = w * kTilePts + q * 32 + lane;
+      if (i >= s0 && i < e0) {
+        lo[0] = min(lo[0], ord_of(x[q])); hi[0] = max(hi[0], ord_of(x[q]));
+        lo[1] = min(lo[1], ord_of(y[q])); hi[1] = max(hi[1], ord_of(y[q]));
+        lo[2] = min(lo[2], ord_of(z[q])); hi[2] = max(hi[2], ord_of(z[q]));
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+      hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+    }
+    const int t = base + j;
+    if (lane == 0 && t < tiles_cap) {
+      tiles[t] = make_int2(s0, e0);
+      tbox[2 * t] = make_float4(float_of(lo[0]), float_of(lo[1]), float_of(lo[2]), 0.f);
+      tbox[2 * t + 1] = make_float4(float_of(hi[0]), float_of(hi[1]), float_of(hi[2]), 0.f);
+      const int b = cloud_of_key(keys[s0], d, mb, B);
+      tcloud[t] = b;
+      if (s0 == 0 || cloud_of_key(keys[s0 - 1], d, mb, B) != b) tfirst[b] = t;
+    }
   }
 }
 
@@ -619,21 +662,25 @@ cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,
   return cudaGetLastError();
 }
 
-cudaError_t launch_tiles(const uint32_t* keys, int64_t n, const Cloud* clouds, int d, int mb,
-                         int B, int n_windows, int* wcnt, int* wbase, int* n_tiles, int2* tiles,
-                         cudaStream_t s) {
-  const int g = (n_windows + 7) / 8;
-  k_tiles_count<<<g, 256, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, wcnt);
-  k_scan_windows<<<1, 1024, 0, s>>>(wcnt, n_windows, wbase, n_tiles);
-  k_tiles_write<<<g, 256, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, wbase, tiles);
+cudaError_t launch_lattice(Cloud* clouds, const CloudRun* crun, int B, int d, int mb,
+                           cudaStream_t s) {
+  k_lattice<<<(B + 255) / 256, 256, 0, s>>>(clouds, crun, B, d, mb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_boxes(const float* xs, const float* ys, const float* zs, int d,
-                              const int2* tiles, int n_tiles, const uint32_t* keys, int mb, int B,
-                              float4* tbox, int* tcloud, int* tfirst, cudaStream_t s) {
-  k_tile_boxes<<<(n_tiles + 7) / 8, 256, 0, s>>>(xs, ys, zs, d, tiles, n_tiles, keys, mb, B, tbox,
-                                                 tcloud, tfirst);
+size_t tiles_scan_words(int n_windows) { return (size_t)(n_windows + 7) / 8 + 1; }
+
+cudaError_t launch_tiles(const uint32_t* keys, int64_t n, Cloud* clouds, int d, int mb, int B,
+                         int cut_div, const unsigned long long* level_hist, int n_windows,
+                         const float* xs, const float* ys, const float* zs,
+                         unsigned long long* scan, int tiles_cap, int2* tiles, float4* tbox,
+                         int* tcloud, int* tfirst, int* n_tiles, DevState* st, cudaStream_t s) {
+  k_choose_levels<<<(B + 255) / 256, 256, 0, s>>>(level_hist, clouds, B, d, mb, cut_div);
+  cudaError_t e = cudaMemsetAsync(scan, 0, sizeof(unsigned long long) * tiles_scan_words(n_windows), s);
+  if (e != cudaSuccess) return e;
+  k_tiles<<<(n_windows + 7) / 8, 256, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, xs, ys, zs,
+                                              scan, tiles_cap, tiles, tbox, tcloud, tfirst,
+                                              n_tiles, st);
   return cudaGetLastError();
 }
 

@@ -49,10 +49,10 @@ def test_aggregate_two_gloo_ranks(tmp_path):
 def test_launch_count():
     sys.path.insert(0, ROOT)
     import bench
-    # setup: reset_boxes, bbox, morton, 3 radix-sort passes, gather, levels,
-    # 3 tiling kernels, tile boxes = 12; run: reset_boxes, bbox, exponents,
+    # setup: reset_boxes, bbox, lattice, morton, 3 radix-sort passes, gather,
+    # levels, choose_levels, tiles = 11; run: reset_boxes, bbox, exponents,
     # reset_run, prep, 3 per pass, finalize, collect, export
-    assert bench.launches_per_step(30) == 12 + 3 + 2 + 90 + 3
+    assert bench.launches_per_step(30) == 11 + 3 + 2 + 90 + 3
 
 
 def test_reference_arm_json_line():
