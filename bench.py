@@ -185,8 +185,8 @@ def run_reference(args):
 def launches_per_step(iters: int) -> int:
     # dkm_setup: reset_boxes, bbox, lattice, morton (with the sort's digit counts), 3
     # one-sweep radix-sort passes over the top 24 key bits, gather, levels, choose_levels,
-    # tiles (ranges and boxes)
-    setup = 2 + 1 + 1 + 3 + 1 + 1 + 1 + 1
+    # tiles (count, scan, ranges and boxes)
+    setup = 2 + 1 + 1 + 3 + 1 + 1 + 1 + 3
     # dkm_run: centroid reset_boxes + bbox + exponents; graph: reset_run, prep,
     # iters x (search, assign, centroids); finalize, collect, export
     run = 3 + 2 + 3 * iters + 3

@@ -167,7 +167,7 @@ struct Layout {
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
   size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_scratch, tbox, tiles,
-      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, tl_scan, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, tl_scratch, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
 };
@@ -205,7 +205,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.tunit = L.take<int>(tm);
   P.cb2 = L.take<float>(k);
   P.tlab = L.take<int>(tm);
-  P.tl_scan = L.take<unsigned long long>(tiles_scan_words((int)nw));
+  P.tl_scratch = L.take<unsigned>(tiles_scratch_words((int)nw));
   P.level_hist = L.take<unsigned long long>(B * (kMaxLevels + 1));
   P.doff = L.take<int64_t>(B + 1);
   P.dcoff = L.take<int64_t>(B + 1);
@@ -637,8 +637,8 @@ dkm_status apply_units(dkm_ctx* c);
 // ranges, boxes, the tile -> cloud map and the tile count (DevState.tiles).
 dkm_status launch_tiling(dkm_ctx* c) {
   DKM_CK(launch_tiles(c->skeys, c->n, c->clouds, c->d, c->mb, c->B, c->cut_div, c->level_hist,
-                      c->n_windows, c->xs, c->ys, c->zs, c->tl_scan, c->tiles_cap, c->tiles,
-                      c->tbox, c->tcloud, c->tfirst, &c->st->tiles, c->st, c->stream));
+                      c->n_windows, c->xs, c->ys, c->zs, c->tl_scratch, c->tiles_cap, c->tiles,
+                      c->tbox, c->tcloud, c->tfirst, &c->st->tiles, c->stream));
   return DKM_OK;
 }
 
@@ -857,7 +857,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->tunit = (int*)(base + P.tunit);
   c->cb2 = (float*)(base + P.cb2);
   c->tlab = (int*)(base + P.tlab);
-  c->tl_scan = (unsigned long long*)(base + P.tl_scan);
+  c->tl_scratch = (unsigned*)(base + P.tl_scratch);
   c->level_hist = (unsigned long long*)(base + P.level_hist);
   c->doff = (int64_t*)(base + P.doff);
   c->dcoff = (int64_t*)(base + P.dcoff);

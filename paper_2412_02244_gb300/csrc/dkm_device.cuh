@@ -53,7 +53,7 @@ struct DevState {
   int passes;            // max over clouds of the passes of the current run
   int err;               // internal error bits (kErr*)
   int label_err;         // dkm_update: a label outside [0, k_b)
-  int sort_err;          // dkm_setup: a look-back (radix sort 1, tiling 2) gave up waiting
+  int sort_err;          // dkm_setup: a radix-sort look-back gave up waiting
   int tiles;             // dkm_setup: tiles of the new point index
   int pad0;
   unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles, last_stays;

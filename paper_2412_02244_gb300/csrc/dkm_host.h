@@ -29,12 +29,12 @@ cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,
                           unsigned long long* hist, cudaStream_t s);
 cudaError_t launch_lattice(Cloud* clouds, const CloudRun* crun, int B, int d, int mb,
                            cudaStream_t s);
-size_t tiles_scan_words(int n_windows);
+size_t tiles_scratch_words(int n_windows);
 cudaError_t launch_tiles(const uint32_t* keys, int64_t n, Cloud* clouds, int d, int mb, int B,
                          int cut_div, const unsigned long long* level_hist, int n_windows,
-                         const float* xs, const float* ys, const float* zs,
-                         unsigned long long* scan, int tiles_cap, int2* tiles, float4* tbox,
-                         int* tcloud, int* tfirst, int* n_tiles, DevState* st, cudaStream_t s);
+                         const float* xs, const float* ys, const float* zs, unsigned* scratch,
+                         int tiles_cap, int2* tiles, float4* tbox, int* tcloud, int* tfirst,
+                         int* n_tiles, cudaStream_t s);
 
 // dkm_iter.cu
 cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s);
@@ -114,7 +114,7 @@ struct dkm_ctx {
   int* tlab = nullptr;         // per tile: single label of its last pass, or -1
   float4* ubox = nullptr;      // per unit box (unit_g > 1)
   int *ucloud = nullptr, *ufirst = nullptr, *tunit = nullptr;
-  unsigned long long* tl_scan = nullptr;   // k_tiles: ticket and look-back words
+  unsigned* tl_scratch = nullptr;   // tiling: cut masks, window counts, CTA totals
   unsigned long long* level_hist = nullptr;
   int64_t *doff = nullptr, *dcoff = nullptr;
   dkm::Cloud* clouds = nullptr;

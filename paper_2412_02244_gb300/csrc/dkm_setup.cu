@@ -21,7 +21,7 @@
 //   k_levels       per cloud, how many Morton cubes each level would cut
 //                  the order into
 //   k_choose_levels  per cloud, the cube level the tiles are cut at
-//   k_tiles        tiles (256-point windows split at cube boundaries) and
+//   k_tiles_*      tiles (256-point windows split at cube boundaries) and
 //                  their AABBs
 #include "dkm_host.h"
 
@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ p, int
 // polls kRsSpinLimit times sets DevState.sort_err and stops.
 // ---------------------------------------------------------------------------
 constexpr int kRsSpinLimit = 1 << 22;
+constexpr int kRsWindow = 16;   // look-back words a sort thread loads per round trip
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
@@ -308,29 +309,9 @@ __global__ void __launch_bounds__(kRsThreads, 3) k_rs_onesweep(
   st_relaxed_u64(my, ((tile == 0 ? tag_incl : tag_own) << 32) | run);
   lbase[d] = block_exclusive_scan256(run, s_warp, nullptr);
   const uint32_t dstart = block_exclusive_scan256(hist[pass * 256 + d], s_warp, nullptr);
-  uint32_t excl = 0;
-  if (tile > 0) {
-    int64_t tt = tile - 1;
-    int polls = 0;
-    while (tt >= 0) {
-      const unsigned long long v = ld_relaxed_u64(status + tt * 256 + d);
-      const unsigned long long tag = v >> 32;
-      if (tag == tag_incl || tag == tag_own) {
-        excl += (uint32_t)v;
-        if (tag == tag_incl) break;
-        --tt;
-        continue;
-      }
-      if (++polls > kRsSpinLimit) {
-        atomicOr(&st->sort_err, 1);
-        break;
-      }
-      if (polls > 8) __nanosleep(64);
-    }
-    st_relaxed_u64(my, (tag_incl << 32) | (excl + run));
-  }
-  goff[d] = dstart + excl;
-  __syncthreads();
+  // lbase and the warp prefixes are visible (barriers in the scan): group
+  // the keys by digit in shared memory now, so that the look-back below runs
+  // with the key registers free
 #pragma unroll
   for (int j = 0; j < kRsItems; ++j) {
     const int64_t i = base + j * 32 + lane;
@@ -341,6 +322,42 @@ __global__ void __launch_bounds__(kRsThreads, 3) k_rs_onesweep(
       sval[loc] = val[j];
     }
   }
+  uint32_t excl = 0;
+  if (tile > 0) {
+    // kRsWindow predecessors per round trip: their words are loaded
+    // together, then consumed nearest first up to an inclusive prefix or
+    // the first word not yet published
+    int64_t tt = tile - 1;
+    int polls = 0;
+    bool done = false;
+    while (!done) {
+      unsigned long long v[kRsWindow];
+#pragma unroll
+      for (int j = 0; j < kRsWindow; ++j)
+        v[j] = tt - j >= 0 ? ld_relaxed_u64(status + (tt - j) * 256 + d) : (tag_incl << 32);
+      int used = 0;
+#pragma unroll
+      for (int j = 0; j < kRsWindow; ++j) {
+        if (done || used < j) break;   // stopped at a word not yet published
+        const unsigned long long tag = v[j] >> 32;
+        if (tag == tag_incl || tag == tag_own) {
+          excl += (uint32_t)v[j];
+          done = tag == tag_incl;
+          used = j + 1;
+        }
+      }
+      tt -= used;
+      if (!done && used == 0) {
+        if (++polls > kRsSpinLimit) {
+          atomicOr(&st->sort_err, 1);
+          break;
+        }
+        if (polls > 8) __nanosleep(64);
+      }
+    }
+    st_relaxed_u64(my, (tag_incl << 32) | (excl + run));
+  }
+  goff[d] = dstart + excl;
   __syncthreads();
   const int cnt = (int)min((int64_t)kRsTile, n - cta0);
   for (int i = threadIdx.x; i < cnt; i += kRsThreads) {
@@ -465,76 +482,96 @@ __global__ void k_choose_levels(const unsigned long long* __restrict__ hist,
   clouds[b].shift = d * (mb - level);
 }
 
-// Tiles, in one kernel.  A CTA (ticket order) takes 8 consecutive
-// 256-windows, one per warp; every window start and every cut position
-// (tile_starts) opens a tile, so a tile never leaves its window.  The CTA
-// counts its tiles, finds the number of tiles before it by decoupled
-// look-back over the lower CTAs (the radix sort's word format, tag 1: own
-// count, tag 2: inclusive prefix; bounded waits set DevState.sort_err bit
-// 2), then each warp writes its tiles' ranges, AABBs (exact min / max of
-// their points), cloud, and each cloud's first tile.  scan[0] holds the
-// ticket and scan[1 + c] CTA c's word; all zeroed beforehand.
-__global__ void __launch_bounds__(256) k_tiles(
-    const uint32_t* __restrict__ keys, int64_t n, const Cloud* __restrict__ clouds, int d, int mb,
-    int B, int n_windows, const float* __restrict__ xs, const float* __restrict__ ys,
-    const float* __restrict__ zs, unsigned long long* scan, int tiles_cap,
-    int2* __restrict__ tiles, float4* __restrict__ tbox, int* __restrict__ tcloud,
-    int* __restrict__ tfirst, int* __restrict__ n_tiles, DevState* st) {
-  __shared__ int s_pos[8][kTilePts + 1];
-  __shared__ int s_cnt[8];
-  __shared__ int s_cta, s_base;
+// Tiles, in three kernels without any inter-CTA wait.  Every window start
+// and every cut position (tile_starts) opens a tile, so a tile never leaves
+// its 256-window.  One warp per window, 8 windows per CTA.
+//   k_tiles_count: per window the 8 ballot masks of its tile starts (mask,
+//     8 words per window) and its tile count (wcnt); per CTA the total (csum).
+//   k_tiles_scan:  exclusive prefix of csum in place (one CTA); the total
+//     tile count.
+//   k_tiles_write: per window its tile ranges from the masks, their AABBs
+//     (exact min / max of their points), clouds, and each cloud's first tile.
+constexpr int kTlWindows = 8;
+
+__global__ void __launch_bounds__(256) k_tiles_count(const uint32_t* __restrict__ keys, int64_t n,
+                                                     const Cloud* __restrict__ clouds, int d,
+                                                     int mb, int B, int n_windows,
+                                                     unsigned* __restrict__ mask,
+                                                     int* __restrict__ wcnt,
+                                                     int* __restrict__ csum) {
+  __shared__ int s_c[kTlWindows];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_cta = (int)atomicAdd((unsigned*)scan, 1u);
-  __syncthreads();
-  const int cta = s_cta;
-  const int64_t w = (int64_t)cta * 8 + wl;
-  const unsigned lt = (1u << lane) - 1u;
+  const int64_t w = (int64_t)blockIdx.x * kTlWindows + wl;
   int c = 0;
   if (w < n_windows) {   // warp-uniform
+    bool f[kTilePts / 32];
+#pragma unroll
     for (int j = 0; j < kTilePts / 32; ++j) {
       const int64_t i = w * kTilePts + j * 32 + lane;
-      const bool f = i < n && tile_starts(keys, i, clouds, d, mb, B);
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (f) s_pos[wl][c + __popc(bal & lt)] = (int)i;
+      f[j] = i < n && tile_starts(keys, i, clouds, d, mb, B);
+    }
+#pragma unroll
+    for (int j = 0; j < kTilePts / 32; ++j) {
+      const unsigned bal = __ballot_sync(0xffffffffu, f[j]);
+      if (lane == j) mask[w * (kTilePts / 32) + j] = bal;
       c += __popc(bal);
     }
-    if (lane == 0) s_pos[wl][c] = (int)min((int64_t)(w + 1) * kTilePts, n);
+    if (lane == 0) wcnt[w] = c;
   }
-  if (lane == 0) s_cnt[wl] = c;
+  if (lane == 0) s_c[wl] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned tot = 0;
-    for (int q = 0; q < 8; ++q) tot += (unsigned)s_cnt[q];
-    unsigned long long* my = scan + 1 + cta;
-    st_relaxed_u64(my, ((cta == 0 ? 2ull : 1ull) << 32) | tot);
-    unsigned excl = 0;
-    if (cta > 0) {
-      int64_t q = cta - 1;
-      int polls = 0;
-      while (q >= 0) {
-        const unsigned long long v = ld_relaxed_u64(scan + 1 + q);
-        const unsigned long long tag = v >> 32;
-        if (tag == 1ull || tag == 2ull) {
-          excl += (unsigned)v;
-          if (tag == 2ull) break;
-          --q;
-          continue;
-        }
-        if (++polls > kRsSpinLimit) {
-          atomicOr(&st->sort_err, 2);
-          break;
-        }
-        if (polls > 8) __nanosleep(64);
-      }
-      st_relaxed_u64(my, (2ull << 32) | (excl + tot));
-    }
-    s_base = (int)excl;
-    if (cta == (int)gridDim.x - 1) *n_tiles = (int)(excl + tot);
+    int t = 0;
+    for (int q = 0; q < kTlWindows; ++q) t += s_c[q];
+    csum[blockIdx.x] = t;
   }
-  __syncthreads();
-  if (w >= n_windows) return;
-  int base = s_base;
-  for (int q = 0; q < wl; ++q) base += s_cnt[q];
+}
+
+__global__ void __launch_bounds__(1024) k_tiles_scan(int* __restrict__ csum, int g,
+                                                     int* __restrict__ n_tiles) {
+  __shared__ int s_w[32];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  int carry = 0;
+  for (int q0 = 0; q0 < g; q0 += 1024) {
+    const int q = q0 + threadIdx.x;
+    const int v = q < g ? csum[q] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wl] = x;
+    __syncthreads();
+    if (wl == 0) {
+      int t = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      s_w[lane] = t;   // inclusive warp totals
+    }
+    __syncthreads();
+    const int before = wl > 0 ? s_w[wl - 1] : 0;
+    if (q < g) csum[q] = carry + before + x - v;
+    carry += s_w[31];
+    __syncthreads();   // s_w is rewritten by the next chunk
+  }
+  if (threadIdx.x == 0) *n_tiles = carry;
+}
+
+__global__ void __launch_bounds__(256) k_tiles_write(
+    const uint32_t* __restrict__ keys, int64_t n, int d, int mb, int B, int n_windows,
+    const float* __restrict__ xs, const float* __restrict__ ys, const float* __restrict__ zs,
+    const unsigned* __restrict__ mask, const int* __restrict__ wcnt, const int* __restrict__ cbase,
+    int tiles_cap, int2* __restrict__ tiles, float4* __restrict__ tbox, int* __restrict__ tcloud,
+    int* __restrict__ tfirst) {
+  __shared__ int s_pos[kTlWindows][kTilePts + 1];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t w0 = (int64_t)blockIdx.x * kTlWindows;
+  const int64_t w = w0 + wl;
+  if (w >= n_windows) return;   // warp-level exit, no CTA barrier below
   constexpr int kPer = kTilePts / 32;
   float x[kPer], y[kPer], z[kPer];
 #pragma unroll
@@ -544,6 +581,20 @@ __global__ void __launch_bounds__(256) k_tiles(
     y[q] = ys[i];
     z[q] = d == 3 ? zs[i] : 0.f;
   }
+  // the tiles of the CTA's earlier windows (lanes 0..7 hold one window each)
+  const int cw = lane < wl && w0 + lane < n_windows ? wcnt[w0 + lane] : 0;
+  const int base = cbase[blockIdx.x] + __reduce_add_sync(0xffffffffu, cw);
+  const unsigned my_mask = lane < kPer ? mask[w * kPer + lane] : 0u;
+  const unsigned lt = (1u << lane) - 1u;
+  int c = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const unsigned bal = __shfl_sync(0xffffffffu, my_mask, j);
+    if (bal & (1u << lane)) s_pos[wl][c + __popc(bal & lt)] = (int)(w * kTilePts + j * 32 + lane);
+    c += __popc(bal);
+  }
+  if (lane == 0) s_pos[wl][c] = (int)min((int64_t)(w + 1) * kTilePts, n);
+  __syncwarp();
   for (int j = 0; j < c; ++j) {
     const int s0 = s_pos[wl][j], e0 = s_pos[wl][j + 1];
     unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
@@ -668,19 +719,27 @@ cudaError_t launch_lattice(Cloud* clouds, const CloudRun* crun, int B, int d, in
   return cudaGetLastError();
 }
 
-size_t tiles_scan_words(int n_windows) { return (size_t)(n_windows + 7) / 8 + 1; }
+// Scratch of the tiling (u32 words): 8 masks per window, the window counts,
+// the per-CTA totals.
+size_t tiles_scratch_words(int n_windows) {
+  return (size_t)n_windows * (kTilePts / 32) + n_windows + (n_windows + kTlWindows - 1) / kTlWindows;
+}
 
 cudaError_t launch_tiles(const uint32_t* keys, int64_t n, Cloud* clouds, int d, int mb, int B,
                          int cut_div, const unsigned long long* level_hist, int n_windows,
-                         const float* xs, const float* ys, const float* zs,
-                         unsigned long long* scan, int tiles_cap, int2* tiles, float4* tbox,
-                         int* tcloud, int* tfirst, int* n_tiles, DevState* st, cudaStream_t s) {
+                         const float* xs, const float* ys, const float* zs, unsigned* scratch,
+                         int tiles_cap, int2* tiles, float4* tbox, int* tcloud, int* tfirst,
+                         int* n_tiles, cudaStream_t s) {
+  unsigned* mask = scratch;
+  int* wcnt = (int*)(mask + (size_t)n_windows * (kTilePts / 32));
+  int* csum = wcnt + n_windows;
+  const int g = (n_windows + kTlWindows - 1) / kTlWindows;
   k_choose_levels<<<(B + 255) / 256, 256, 0, s>>>(level_hist, clouds, B, d, mb, cut_div);
-  cudaError_t e = cudaMemsetAsync(scan, 0, sizeof(unsigned long long) * tiles_scan_words(n_windows), s);
-  if (e != cudaSuccess) return e;
-  k_tiles<<<(n_windows + 7) / 8, 256, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, xs, ys, zs,
-                                              scan, tiles_cap, tiles, tbox, tcloud, tfirst,
-                                              n_tiles, st);
+  k_tiles_count<<<g, 32 * kTlWindows, 0, s>>>(keys, n, clouds, d, mb, B, n_windows, mask, wcnt,
+                                              csum);
+  k_tiles_scan<<<1, 1024, 0, s>>>(csum, g, n_tiles);
+  k_tiles_write<<<g, 32 * kTlWindows, 0, s>>>(keys, n, d, mb, B, n_windows, xs, ys, zs, mask,
+                                              wcnt, csum, tiles_cap, tiles, tbox, tcloud, tfirst);
   return cudaGetLastError();
 }
 

@@ -50,9 +50,9 @@ def test_launch_count():
     sys.path.insert(0, ROOT)
     import bench
     # setup: reset_boxes, bbox, lattice, morton, 3 radix-sort passes, gather,
-    # levels, choose_levels, tiles = 11; run: reset_boxes, bbox, exponents,
-    # reset_run, prep, 3 per pass, finalize, collect, export
-    assert bench.launches_per_step(30) == 11 + 3 + 2 + 90 + 3
+    # levels, choose_levels, 3 tiling kernels = 13; run: reset_boxes, bbox,
+    # exponents, reset_run, prep, 3 per pass, finalize, collect, export
+    assert bench.launches_per_step(30) == 13 + 3 + 2 + 90 + 3
 
 
 def test_reference_arm_json_line():
