@@ -271,6 +271,45 @@ __device__ __forceinline__ float maxd2(const float4& lo, const float4& hi, float
   return s;
 }
 
+// Dominance over a box (the filtering test of kd-tree k-means): c cannot be
+// the nearest centroid of any point of the box [lo, hi] when every point of
+// the box is closer to r.  d^2(p, r) - d^2(p, c) is linear in p, so its
+// maximum over the box sits at the vertex that takes, per axis, the face
+// toward c; c is dominated when d^2(v, c) - d^2(v, r) exceeds the margin
+// kDom * (maxd^2(box, r) + maxd^2(box, c)).  That margin covers the FP32
+// rounding of the distances compared here and of the assignment's own d^2
+// (about 5 ulp relative each; 2^-17 leaves a 10x margin), so a tie that
+// the lowest index could decide for c is never pruned.  `slack` is the
+// margin or any upper bound of it (dom_slack).
+constexpr float kDom = 7.62939453125e-06f;   // 2^-17
+
+__device__ __forceinline__ bool dominated(const float4& lo, const float4& hi, const float4& r,
+                                          float slack, float cx, float cy, float cz, int d) {
+  const float vx = cx > r.x ? hi.x : lo.x;
+  const float vy = cy > r.y ? hi.y : lo.y;
+  const float ax = __fsub_rn(vx, r.x), ay = __fsub_rn(vy, r.y);
+  const float bx = __fsub_rn(vx, cx), by = __fsub_rn(vy, cy);
+  float dr = __fmaf_rn(ay, ay, __fmul_rn(ax, ax));
+  float dc = __fmaf_rn(by, by, __fmul_rn(bx, bx));
+  if (d == 3) {
+    const float vz = cz > r.z ? hi.z : lo.z;
+    const float az = __fsub_rn(vz, r.z), bz = __fsub_rn(vz, cz);
+    dr = __fmaf_rn(az, az, dr);
+    dc = __fmaf_rn(bz, bz, dc);
+  }
+  return __fsub_rn(dc, dr) > slack;
+}
+
+// A margin bound for every candidate c of a box with mind^2(box, c) <= u2k,
+// against a reference with maxd^2(box, r) = r_maxd2: maxd(box, c) <=
+// mind(box, c) + diam(box), so maxd^2(box, c) <= 2 u2k + 2 diam^2.
+__device__ __forceinline__ float dom_slack(const float4& lo, const float4& hi, float r_maxd2,
+                                           float u2k, int d) {
+  const float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = d == 3 ? hi.z - lo.z : 0.f;
+  const float diam2 = ex * ex + ey * ey + ez * ez;
+  return 1.0001f * kDom * (r_maxd2 + 2.f * u2k + 2.f * diam2);
+}
+
 // Cell coordinate of x along one axis (monotone in x; clamped).
 // A NaN maps to cell 0, so a bad centroid can never index out of the grid.
 __device__ __forceinline__ int cell_coord(float x, float g0, float inv_s, int dim) {

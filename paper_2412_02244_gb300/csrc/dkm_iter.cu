@@ -213,13 +213,16 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
 //            overflow list.  The true nearest centroid of each point in the
 //            box always passes (its distance is <= the distance to the
 //            U-defining centroid <= U): the ball-node test of Section II-B /
-//            IV-A with boxes in place of balls.
+//            IV-A with boxes in place of balls.  A centroid that passes is
+//            still dropped when the U-defining centroid r1 dominates it over
+//            the whole box (dominated(): every point of the box is closer
+//            to r1), which no nearest centroid can be.
 // The list is written unordered; k_assign picks the lexicographic minimum
 // of (d^2, id), which does not depend on the order.
 // ---------------------------------------------------------------------------
 constexpr int kSearchWarps = 2;   // independent warps: small CTAs free SM slots early
 #ifndef DKM_SEARCH_MIN_BLOCKS
-#define DKM_SEARCH_MIN_BLOCKS 24   // 40 registers: more resident warps hide the dependent loads
+#define DKM_SEARCH_MIN_BLOCKS 20   // 48 registers: many resident warps hide the dependent loads
 #endif
 
 __device__ __forceinline__ long long cell_index(const Grid& G, int cx, int cy, int cz) {
@@ -300,13 +303,17 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   // ids of this cloud near the tile (lists are cleared whenever the tiles
   // change), so its current positions give U in one load round; without a
   // list, rings of cells around the box are scanned.
+  // The centroid that gives U (r1) also serves as the dominance reference
+  // of phase B.
   float u2 = INFINITY;
+  float m = INFINITY;
+  float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f);   // this lane's best so far
   const int q_old = A.tcnt[t];
   if (q_old >= 1 && q_old <= kTileCap) {
-    float m = INFINITY;
     for (int j = lane; j < q_old; j += 32) {
       const float4 c = A.cw[__float_as_int(out[j].w)];
-      m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
+      const float mc = maxd2(lo, hi, c.x, c.y, c.z, d);
+      if (mc < m) { m = mc; r1 = c; }
     }
     u2 = warp_min_nonneg(m);   // every lane has read its old ids before any is overwritten
   }
@@ -320,11 +327,11 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
       whole = whole && rlo[a] == 0 && rhi[a] == G.dims[a] - 1;
       ncell *= (long long)(rhi[a] - rlo[a] + 1);
     }
-    float m = INFINITY;
     if (ncell > flat_cells) {
       for (int j = c0 + lane; j < c1; j += 32) {
         const float4 c = A.cw[j];
-        m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
+        const float mc = maxd2(lo, hi, c.x, c.y, c.z, d);
+        if (mc < m) { m = mc; r1 = c; }
       }
       u2 = warp_min_nonneg(m);
       break;
@@ -337,12 +344,14 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
       int cnt = min(gcnt[cell], kBucketCap);
       for (int i = 0; i < cnt; ++i) {
         const float4 e = gbkt[cell * kBucketCap + i];
-        m = fminf(m, maxd2(lo, hi, e.x, e.y, e.z, d));
+        const float mc = maxd2(lo, hi, e.x, e.y, e.z, d);
+        if (mc < m) { m = mc; r1 = e; }
       }
     }
     for (int q = lane; q < n_ovf; q += 32) {
-      float4 c = ovf[q];
-      m = fminf(m, maxd2(lo, hi, c.x, c.y, c.z, d));
+      const float4 c = ovf[q];
+      const float mc = maxd2(lo, hi, c.x, c.y, c.z, d);
+      if (mc < m) { m = mc; r1 = c; }
     }
     u2 = warp_min_nonneg(m);
     if (u2 < INFINITY || whole) break;
@@ -355,8 +364,19 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
     return;
   }
 
+  // r1 = a centroid with maxd^2 = u2 (the lowest such lane's)
+  {
+    const int src = __ffs(__ballot_sync(0xffffffffu, m == u2)) - 1;
+    r1.x = __shfl_sync(0xffffffffu, r1.x, src);
+    r1.y = __shfl_sync(0xffffffffu, r1.y, src);
+    r1.z = __shfl_sync(0xffffffffu, r1.z, src);
+  }
+
   // ---- phase B ----
+  // keep: within the ball bound (mind^2 <= U^2 kKeep) and not dominated
+  // over the box by r1
   const float u2k = u2 * kKeep;
+  const float slack = dom_slack(lo, hi, u2, u2k, d);
   float mag = fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y)));
   if (d == 3) mag = fmaxf(mag, fmaxf(fabsf(lo.z), fabsf(hi.z)));
   const float ul = sqrtf(u2k) * 1.00002f + 1e-5f * mag + 1e-30f;
@@ -379,7 +399,8 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
       bool keep = false;
       if (j < c1) {
         c = A.cw[j];
-        keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k;
+        keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k &&
+               !dominated(lo, hi, r1, slack, c.x, c.y, c.z, d);
       }
       unsigned bal = __ballot_sync(0xffffffffu, keep);
       int pos = count + __popc(bal & lt);
@@ -401,7 +422,8 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
       for (int i = 0; i < cmax; ++i) {
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < cnt) e = gbkt[cell * kBucketCap + i];
-        const bool keep = i < cnt && mind2(lo, hi, e.x, e.y, e.z, d) <= u2k;
+        const bool keep = i < cnt && mind2(lo, hi, e.x, e.y, e.z, d) <= u2k &&
+                          !dominated(lo, hi, r1, slack, e.x, e.y, e.z, d);
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         int pos = count + __popc(bal & lt);
         if (keep && pos < kTileCap) out[pos] = e;
@@ -414,7 +436,8 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
       bool keep = false;
       if (q < n_ovf) {
         c = ovf[q];
-        keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k;
+        keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k &&
+               !dominated(lo, hi, r1, slack, c.x, c.y, c.z, d);
       }
       unsigned bal = __ballot_sync(0xffffffffu, keep);
       int pos = count + __popc(bal & lt);
