@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "37c5c7b6d6a38189", "bytes_per_launch": 132_628_480 + 22_285_056,
+NCU_TRAFFIC = {"sha": "f5e7fd7df4a08f3a", "bytes_per_launch": 129_725_952 + 22_583_296,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
