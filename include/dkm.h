@@ -146,7 +146,8 @@ DKM_API dkm_status dkm_plan(int64_t n, int d, int k, const float* bbox_lo, const
  * (n x d).  The library keeps its own sorted copy; the caller may free
  * points afterwards.  opts may be NULL (defaults).
  * Errors: DKM_EINVAL (d not 2/3, n < 1, k < 1, k > n, null pointer,
- * non-finite point), DKM_ENOMEM, DKM_ECUDA.  On error *out is NULL.
+ * non-finite point), DKM_ENOMEM, DKM_ECUDA, DKM_ETIMEOUT (as dkm_setup).
+ * On error *out is NULL.
  */
 DKM_API dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int d, int k,
                       const dkm_options* opts);
@@ -155,7 +156,10 @@ DKM_API dkm_status dkm_create(dkm_ctx** out, const float* points, int64_t n, int
  * Rebuild the point index (bounding box, Morton sort into tiles, tile
  * boxes -- the analog of building the spatial-vector Ball-tree once,
  * Algorithm 1 first step) for a new set of n x d points of the context's
- * size.  Errors: DKM_EINVAL (null, non-finite), DKM_ECUDA.
+ * size.  Errors: DKM_EINVAL (null, non-finite), DKM_ECUDA, DKM_ETIMEOUT
+ * (a radix-sort pass waits, with a bounded number of polls, for the
+ * digit counts of the CTAs before it; it gave up -- the context then needs
+ * a new dkm_setup).
  */
 DKM_API dkm_status dkm_setup(dkm_ctx* ctx, const float* points);
 
@@ -417,6 +421,19 @@ DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int
 DKM_API dkm_status dkm_lloyd_step_noalloc(const float* points, int64_t n, int d, int k,
                                           const float* centroids, float* centroids_out,
                                           int32_t* labels, double* sse_out, void* stream);
+
+/*
+ * Self-test of the library's one device-side wait: the radix sort of
+ * dkm_setup, whose CTAs wait (decoupled look-back) for the digit counts of
+ * the CTAs before them.  Runs one sort pass on 8,192 keys whose only CTA
+ * is handed the second tile, so the count it waits for is never published:
+ * the wait must give up by itself (after about a second) and report it.
+ * Allocates and frees its own small device buffers on a private stream.
+ * seconds_out (nullable, host): the wall time of the pass.
+ * Returns DKM_OK if the wait ended and was reported; DKM_EINTERNAL if the
+ * pass ended without reporting; DKM_ECUDA.
+ */
+DKM_API dkm_status dkm_selftest_wait(double* seconds_out);
 
 #ifdef __cplusplus
 }

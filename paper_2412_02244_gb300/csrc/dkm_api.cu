@@ -4,6 +4,7 @@
 // planner (the memory-tunable index of Section V-A), and the Lloyd loop of
 // Algorithm 1 captured once per (context, max_iter) as a CUDA graph.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -645,7 +646,7 @@ dkm_status launch_tiling(dkm_ctx* c) {
 // Host side of a tiling, from the synchronised DevState and cloud table
 // (pinned copies): the cut shifts and the tile count.
 dkm_status finish_tiling(dkm_ctx* c, const DevState& h, const Cloud* dev_clouds) {
-  if (h.sort_err) return fail(DKM_EINTERNAL, "index build: a look-back wait timed out");
+  if (h.sort_err) return fail(DKM_ETIMEOUT, "index build: a radix-sort look-back wait timed out");
   for (int b = 0; b < c->B; ++b) c->h_clouds[b].shift = dev_clouds[b].shift;
   c->tile_level = c->mb - c->h_clouds[0].shift / c->d;
   const int nt = h.tiles;
@@ -1243,6 +1244,41 @@ const char* dkm_status_string(dkm_status s) {
 }
 
 const char* dkm_last_error(void) { return g_last_error.c_str(); }
+
+dkm_status dkm_selftest_wait(double* seconds_out) {
+  const int64_t n = 8192;
+  void* buf = nullptr;
+  const size_t key_bytes = sizeof(uint32_t) * n;
+  const size_t scratch = rs_scratch_bytes(n);
+  const size_t total = 4 * key_bytes + scratch + sizeof(DevState);
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(DKM_ECUDA, "cudaStreamCreate failed");
+  if (cudaMalloc(&buf, total) != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return fail(DKM_ECUDA, "cudaMalloc failed");
+  }
+  char* base = (char*)buf;
+  uint32_t* keys[2] = {(uint32_t*)base, (uint32_t*)(base + key_bytes)};
+  uint32_t* vals[2] = {(uint32_t*)(base + 2 * key_bytes), (uint32_t*)(base + 3 * key_bytes)};
+  void* scr = base + 4 * key_bytes;
+  DevState* st = (DevState*)(base + 4 * key_bytes + scratch);   // scratch is a multiple of 8
+  dkm_status r = DKM_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaMemsetAsync(buf, 0, total, s);
+  if (e == cudaSuccess) e = launch_sort_wait_selftest(keys, vals, n, scr, st, s);
+  const double sec =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int flag = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&flag, &st->sort_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) r = fail(DKM_ECUDA, "self-test: %s", cudaGetErrorString(e));
+  else if (!flag) r = fail(DKM_EINTERNAL, "self-test: the wait ended without reporting");
+  if (seconds_out) *seconds_out = sec;
+  cudaFree(buf);
+  cudaStreamDestroy(s);
+  return r;
+}
 
 dkm_status dkm_plan(int64_t n, int d, int k, const float* bbox_lo, const float* bbox_hi,
                     const dkm_options* opts, dkm_plan_info* out) {

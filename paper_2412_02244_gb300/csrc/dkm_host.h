@@ -23,6 +23,8 @@ size_t rs_scratch_bytes(int64_t n);
 cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, int bits_lo,
                               int bits_hi, void* scratch, DevState* st, int* final_buf,
                               cudaStream_t s);
+cudaError_t launch_sort_wait_selftest(uint32_t* keys[2], uint32_t* vals[2], int64_t n,
+                                      void* scratch, DevState* st, cudaStream_t s);
 cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,
                           float* ys, float* zs, int64_t n_pad, cudaStream_t s);
 cudaError_t launch_levels(const uint32_t* keys, int64_t n, int d, int mb, int B,

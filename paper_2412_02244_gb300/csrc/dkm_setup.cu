@@ -207,9 +207,17 @@ __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ p, int
 // including the tile), the count in the low 32 bits.  The buffer is zeroed
 // once per sort; a word left by an earlier pass carries an older tag and
 // reads as "not yet published".  Every wait is bounded: a look-back that
-// polls kRsSpinLimit times sets DevState.sort_err and stops.
+// has waited kRsWaitNs (or polled kRsSpinLimit times) sets DevState.sort_err
+// and stops; the scatter then only writes inside the array.
 // ---------------------------------------------------------------------------
-constexpr int kRsSpinLimit = 1 << 22;
+constexpr int kRsSpinLimit = 1 << 24;                     // polls (second bound)
+constexpr unsigned long long kRsWaitNs = 1000000000ull;   // 1 s of waiting
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 constexpr int kRsWindow = 16;   // look-back words a sort thread loads per round trip
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
@@ -329,6 +337,7 @@ __global__ void __launch_bounds__(kRsThreads, 3) k_rs_onesweep(
     // the first word not yet published
     int64_t tt = tile - 1;
     int polls = 0;
+    unsigned long long t0 = 0;
     bool done = false;
     while (!done) {
       unsigned long long v[kRsWindow];
@@ -348,7 +357,8 @@ __global__ void __launch_bounds__(kRsThreads, 3) k_rs_onesweep(
       }
       tt -= used;
       if (!done && used == 0) {
-        if (++polls > kRsSpinLimit) {
+        if (polls == 0) t0 = global_ns();
+        if (++polls > kRsSpinLimit || global_ns() - t0 > kRsWaitNs) {
           atomicOr(&st->sort_err, 1);
           break;
         }
@@ -689,6 +699,27 @@ cudaError_t launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, i
   }
   *final_buf = cur;
   return cudaGetLastError();
+}
+
+// Self-test of the bounded wait: one radix pass over n keys whose only CTA
+// is handed tile 1 (the ticket starts at 1), so it waits for tile 0, which
+// never runs; the wait must end by itself and set DevState.sort_err.
+cudaError_t launch_sort_wait_selftest(uint32_t* keys[2], uint32_t* vals[2], int64_t n,
+                                      void* scratch, DevState* st, cudaStream_t s) {
+  if (n < 2 * (int64_t)kRsTile) return cudaErrorInvalidValue;
+  uint32_t* hist = (uint32_t*)scratch;
+  uint32_t* ticket = hist + kRsMaxPasses * 256;
+  unsigned long long* status = (unsigned long long*)(hist + kRsHistWords);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, rs_scratch_bytes(n), s);
+  if (e != cudaSuccess) return e;
+  const uint32_t one = 1;
+  e = cudaMemcpyAsync(ticket, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  k_rs_onesweep<<<1, kRsThreads, 0, s>>>(keys[0], nullptr, keys[1], vals[1], n, 0, 0, hist,
+                                         status, ticket, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);   // `one` lives on this stack frame
 }
 
 cudaError_t launch_gather(const float* p, int64_t n, int d, const uint32_t* order, float* xs,

@@ -127,6 +127,7 @@ _SIGS = [
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    ("dkm_selftest_wait", ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     ("dkm_hard_sse", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -443,6 +444,15 @@ def dkm_hard_sse(points, offsets, B: int, d: int, k: int, centroids, labels=None
     gc, _k6 = _arr(grad_centroids, "float32", B * k * d, "grad_centroids")
     _check(lib().dkm_hard_sse(p, off, B, d, k, c, lab, ls, gp, gc, ctypes.c_void_p(stream or 0)),
            "dkm_hard_sse")
+
+
+def dkm_selftest_wait() -> float:
+    """Run the self-test of the radix sort's bounded wait (one pass whose
+    awaited count is never published); raises unless the wait gave up by
+    itself and reported it.  Returns the pass's wall time in seconds."""
+    sec = ctypes.c_double()
+    _check(lib().dkm_selftest_wait(ctypes.byref(sec)), "dkm_selftest_wait")
+    return sec.value
 
 
 def dkm_lloyd_step_noalloc(points, n: int, d: int, k: int, centroids, centroids_out, labels,

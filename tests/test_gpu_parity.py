@@ -316,3 +316,17 @@ def test_run_graph_reuse_across_setups(dkm):
     fresh = gpu_run(dkm, make_ctx(dkm, b.points, b.k, early_stop=0), b.init, 7)
     for x, y in zip(moved, fresh):
         assert np.array_equal(x, y)
+
+
+def test_bounded_sort_wait_gives_up_and_the_device_stays_usable(dkm):
+    """The radix sort of dkm_setup is the library's one device-side wait
+    (decoupled look-back).  Its self-test hands the only CTA of a pass the
+    second tile, so the count it waits for is never published: the wait
+    must end by itself after about a second and report it, and the device
+    must keep working (a full fit afterwards matches the oracle)."""
+    sec = dkm.dkm_selftest_wait()
+    assert 0.5 < sec < 30.0
+    w = synth.lidar3d(seed=73, n=20_011, k=40, n_objects=10)
+    lab_o, best, second = oracle_pkg.get().assign(w.points, w.init)
+    lab_g, sse_g, _ = gpu_assign(dkm, make_ctx(dkm, w.points, w.k), w.init)
+    check_labels(lab_g, lab_o, best, second)
