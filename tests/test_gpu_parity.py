@@ -330,3 +330,30 @@ def test_bounded_sort_wait_gives_up_and_the_device_stays_usable(dkm):
     lab_o, best, second = oracle_pkg.get().assign(w.points, w.init)
     lab_g, sse_g, _ = gpu_assign(dkm, make_ctx(dkm, w.points, w.k), w.init)
     check_labels(lab_g, lab_o, best, second)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_exact_ties_survive_pruning(dkm, oracle, d):
+    """Points and centroids on integer lattices, so every d^2 is exact in
+    FP32 and FP64: each point with an odd coordinate is exactly equidistant
+    from 2, 4 or 8 centroids, and the centroid order is shuffled, so the
+    lowest index is spatially arbitrary; some centroids are duplicated.
+    The ball bound and the dominance test must keep every tied centroid
+    that the lowest index decides for: labels equal brute force and the
+    oracle exactly, with no near-tie allowance."""
+    rng = np.random.default_rng(11 + d)
+    g = np.arange(0, 48, 2, dtype=np.float32)
+    axes = [g, g] if d == 2 else [g, g, g[:6]]
+    C = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, d)
+    C = np.concatenate([C, C[rng.choice(len(C), 40, replace=False)]])   # duplicates
+    C = np.ascontiguousarray(C[rng.permutation(len(C))])
+    q = np.arange(0, 47, dtype=np.float32)
+    paxes = [q, q] if d == 2 else [q, q, q[:11]]
+    P = np.stack(np.meshgrid(*paxes, indexing="ij"), -1).reshape(-1, d)
+    P = np.ascontiguousarray(P[rng.permutation(len(P))])
+    k = len(C)
+    lab_o, best, second = oracle.assign(P, C)
+    assert np.count_nonzero(best == second) > len(P) // 4   # many exact ties
+    for algo in (dkm.DKM_ALGO_INDEXED, dkm.DKM_ALGO_BRUTE):
+        lab_g, _, _ = gpu_assign(dkm, make_ctx(dkm, P, k, algo=algo), C)
+        assert np.array_equal(lab_g, lab_o)
