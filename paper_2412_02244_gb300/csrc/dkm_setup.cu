@@ -31,6 +31,9 @@ constexpr int kRsThreads = 256;
 constexpr int kRsItems = 16;
 constexpr int kRsTile = kRsThreads * kRsItems;   // 4096 keys per CTA of the sort
 constexpr int kRsMaxPasses = 4;                  // 8-bit digits of a 32-bit key
+#ifndef DKM_RS_MIN_BLOCKS
+#define DKM_RS_MIN_BLOCKS 3   // resident sort CTAs per SM (80 registers)
+#endif
 constexpr float kMaxAbsCoord = 1.0e18f;          // larger coordinates are rejected
 
 // ---------------------------------------------------------------------------
@@ -51,6 +54,18 @@ __device__ __forceinline__ int seg_of(const int64_t* __restrict__ seg, int B, in
 // (seg, B + 1 entries): blockIdx.y = cloud, blockIdx.x strides over its
 // rows.  which = 0 -> CloudRun.pbox, 1 -> CloudRun.cbox.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void bbox_add(float v, int a, float (&lo)[3], float (&hi)[3], int& bad) {
+  if (!(fabsf(v) <= kMaxAbsCoord)) {   // also catches NaN
+    bad = 1;
+  } else {
+    lo[a] = fminf(lo[a], v);
+    hi[a] = fmaxf(hi[a], v);
+  }
+}
+
+// Rows are read in aligned groups of G = 4 (3D) or 2 (2D) rows, 16-byte
+// loads of 12 or 4 floats, when the array is 16-byte aligned; the rows
+// before the first and after the last whole group are read one by one.
 __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int d,
                                               const int64_t* __restrict__ seg, CloudRun* crun,
                                               DevState* st, int which) {
@@ -59,16 +74,35 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int d
   float lo[3] = {INFINITY, INFINITY, INFINITY};
   float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   int bad = 0;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += stride) {
-    for (int a = 0; a < d; ++a) {
-      float v = p[i * d + a];
-      if (!(fabsf(v) <= kMaxAbsCoord)) {   // also catches NaN
-        bad = 1;
-      } else {
-        lo[a] = fminf(lo[a], v);
-        hi[a] = fmaxf(hi[a], v);
-      }
+  const int G = d == 3 ? 4 : 2;
+  int64_t ra = r0, rb = r0;   // whole groups cover [ra, rb)
+#ifndef DKM_SCALAR_SETUP
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    ra = min(r1, (r0 + G - 1) / G * G);
+    rb = ra + (r1 - ra) / G * G;
+  }
+#endif
+  for (int64_t i = r0 + gt; i < r1; i += stride) {   // the rows outside the groups
+    if (i >= ra && i < rb) continue;
+    bbox_add(p[i * d], 0, lo, hi, bad);
+    bbox_add(p[i * d + 1], 1, lo, hi, bad);
+    if (d == 3) bbox_add(p[i * d + 2], 2, lo, hi, bad);
+  }
+  const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+  for (int64_t q = ra / G + gt; q < rb / G; q += stride) {
+    if (d == 3) {
+      const float4 u = p4[3 * q], v = p4[3 * q + 1], w = p4[3 * q + 2];
+      const float f[12] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int e = 0; e < 12; ++e) bbox_add(f[e], e % 3, lo, hi, bad);
+    } else {
+      const float4 u = p4[q];
+      bbox_add(u.x, 0, lo, hi, bad);
+      bbox_add(u.y, 1, lo, hi, bad);
+      bbox_add(u.z, 0, lo, hi, bad);
+      bbox_add(u.w, 1, lo, hi, bad);
     }
   }
   for (int a = 0; a < 3; ++a) {
@@ -80,8 +114,9 @@ __global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ p, int d
   bad = __reduce_or_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
     unsigned* box = which == 0 ? crun[b].pbox : crun[b].cbox;
-    for (int a = 0; a < d; ++a) {
-      if (lo[a] <= hi[a]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < d && lo[a] <= hi[a]) {
         atomicMin(&box[a], ord_of(lo[a]));
         atomicMax(&box[3 + a], ord_of(hi[a]));
       }
@@ -142,10 +177,30 @@ __device__ __forceinline__ uint32_t spread2(uint32_t v) {   // 15 bits -> every 
 
 // Key of a point of cloud b: b in the bits above d * mb, then the Morton
 // code of its mb-bit-per-axis lattice coordinates on the cloud's own box.
-// The CTA also counts, for each of the npass sort passes, how many keys
-// have each 8-bit digit (key >> (shift0 + 8 q)) & 255 (hist, npass x 256,
-// zeroed beforehand).  A warp whose 32 keys share a digit adds 32 once,
-// which keeps spatially coherent input free of shared-memory contention.
+__device__ __forceinline__ uint32_t morton_key(float x, float y, float z, int d, int b, int B,
+                                               const Cloud& c, int mb) {
+  const float qmax = (float)((1u << mb) - 1u);
+  const float inv = c.minv;
+  const float q0 = fminf(fmaxf((x - c.mlo[0]) * inv, 0.f), qmax);
+  const float q1 = fminf(fmaxf((y - c.mlo[1]) * inv, 0.f), qmax);
+  uint32_t key;
+  if (d == 3) {
+    const float q2 = fminf(fmaxf((z - c.mlo[2]) * inv, 0.f), qmax);
+    key = spread3((uint32_t)q0) | (spread3((uint32_t)q1) << 1) | (spread3((uint32_t)q2) << 2);
+  } else {
+    key = spread2((uint32_t)q0) | (spread2((uint32_t)q1) << 1);
+  }
+  if (B > 1) key |= (uint32_t)b << (d * mb);
+  return key;
+}
+
+// The keys of all points.  A thread takes G consecutive rows (4 in 3D, 2 in
+// 2D: 16-byte loads of 12 or 4 floats and one 16- or 8-byte key store) when
+// the array is 16-byte aligned, else one row.  The CTA also counts, for
+// each of the npass sort passes, how many keys have each 8-bit digit
+// (key >> (shift0 + 8 q)) & 255 (hist, npass x 256, zeroed beforehand).  A
+// warp whose 32 keys share a digit adds 32 once, which keeps spatially
+// coherent input free of shared-memory contention.
 __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ p, int64_t n, int d,
                                                 const int64_t* __restrict__ seg, int B,
                                                 const Cloud* __restrict__ clouds, int mb,
@@ -155,35 +210,74 @@ __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ p, int
   for (int t = threadIdx.x; t < kRsMaxPasses * 256; t += blockDim.x) (&h[0][0])[t] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const float qmax = (float)((1u << mb) - 1u);
+  int G = 1;
+#ifndef DKM_SCALAR_SETUP
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) G = d == 3 ? 4 : 2;
+#endif
+  const int64_t ng = (n + G - 1) / G;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // the loop bound is uniform over the CTA: every lane takes part in the votes
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-    const int64_t i = i0 + threadIdx.x;
-    const bool v = i < n;
-    uint32_t key = 0;
-    if (v) {
-      const int b = B > 1 ? seg_of(seg, B, i) : 0;
-      const Cloud& c = clouds[b];
-      const float inv = c.minv;
-      const float q0 = fminf(fmaxf((p[i * d + 0] - c.mlo[0]) * inv, 0.f), qmax);
-      const float q1 = fminf(fmaxf((p[i * d + 1] - c.mlo[1]) * inv, 0.f), qmax);
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x; q0 < ng; q0 += stride) {
+    const int64_t q = q0 + threadIdx.x;
+    uint32_t key[4] = {0u, 0u, 0u, 0u};
+    bool v[4] = {false, false, false, false};
+    if (G > 1 && (q + 1) * G <= n) {   // a whole aligned group
+      const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+      float f[12];
       if (d == 3) {
-        const float q2 = fminf(fmaxf((p[i * d + 2] - c.mlo[2]) * inv, 0.f), qmax);
-        key = spread3((uint32_t)q0) | (spread3((uint32_t)q1) << 1) | (spread3((uint32_t)q2) << 2);
+        const float4 u = p4[3 * q], w1 = p4[3 * q + 1], w2 = p4[3 * q + 2];
+        f[0] = u.x; f[1] = u.y; f[2] = u.z; f[3] = u.w; f[4] = w1.x; f[5] = w1.y;
+        f[6] = w1.z; f[7] = w1.w; f[8] = w2.x; f[9] = w2.y; f[10] = w2.z; f[11] = w2.w;
       } else {
-        key = spread2((uint32_t)q0) | (spread2((uint32_t)q1) << 1);
+        const float4 u = p4[q];
+        f[0] = u.x; f[1] = u.y; f[2] = u.z; f[3] = u.w;
       }
-      if (B > 1) key |= (uint32_t)b << (d * mb);
-      keys[i] = key;
+      if (d == 3) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int64_t i = q * 4 + r;
+          const int b = B > 1 ? seg_of(seg, B, i) : 0;
+          key[r] = morton_key(f[3 * r], f[3 * r + 1], f[3 * r + 2], 3, b, B, clouds[b], mb);
+          v[r] = true;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int64_t i = q * 2 + r;
+          const int b = B > 1 ? seg_of(seg, B, i) : 0;
+          key[r] = morton_key(f[2 * r], f[2 * r + 1], 0.f, 2, b, B, clouds[b], mb);
+          v[r] = true;
+        }
+      }
+      if (d == 3) {
+        reinterpret_cast<uint4*>(keys)[q] = make_uint4(key[0], key[1], key[2], key[3]);
+      } else {
+        reinterpret_cast<uint2*>(keys)[q] = make_uint2(key[0], key[1]);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t i = q * G + r;
+        if (r < G && i < n) {
+          const int b = B > 1 ? seg_of(seg, B, i) : 0;
+          key[r] = morton_key(p[i * d], p[i * d + 1], d == 3 ? p[i * d + 2] : 0.f, d, b, B,
+                              clouds[b], mb);
+          v[r] = true;
+          keys[i] = key[r];
+        }
+      }
     }
-    for (int q = 0; q < npass; ++q) {
-      const uint32_t dig = (key >> (shift0 + 8 * q)) & 0xffu;
-      const uint32_t d0 = __shfl_sync(0xffffffffu, dig, 0);
-      if (__all_sync(0xffffffffu, v && dig == d0)) {
-        if (lane == 0) atomicAdd(&h[q][d0], 32u);
-      } else if (v) {
-        atomicAdd(&h[q][dig], 1u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= G) break;   // G is uniform
+      for (int pq = 0; pq < npass; ++pq) {
+        const uint32_t dig = (key[r] >> (shift0 + 8 * pq)) & 0xffu;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dig, 0);
+        if (__all_sync(0xffffffffu, v[r] && dig == d0)) {
+          if (lane == 0) atomicAdd(&h[pq][d0], 32u);
+        } else if (v[r]) {
+          atomicAdd(&h[pq][dig], 1u);
+        }
       }
     }
   }
@@ -263,7 +357,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t v, uint32_t
 // item, lane order, which is the input order), placed in shared memory
 // grouped by digit, then written out digit run by digit run so that
 // consecutive threads store to consecutive addresses.
-__global__ void __launch_bounds__(kRsThreads, 3) k_rs_onesweep(
+__global__ void __launch_bounds__(kRsThreads, DKM_RS_MIN_BLOCKS) k_rs_onesweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, int pass,
     const uint32_t* __restrict__ hist, unsigned long long* status, uint32_t* ticket,
