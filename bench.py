@@ -259,7 +259,7 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
     ini = torch.from_numpy(init).to(dev)
     C = torch.empty(K * 3, dtype=torch.float32, device=dev)
     lab = torch.empty(n, dtype=torch.int32, device=dev)
-    opts = dkm.dkm_default_options(early_stop=0, profile=1, stream=stream.cuda_stream)
+    opts = dkm.dkm_default_options(early_stop=0, profile=it, stream=stream.cuda_stream)
     ctx = dkm.dkm_create_batched(pts, off, 3, ks, opts)
     tune = dkm.dkm_autotune(ctx, ini, passes=3, use_cache=False)
 
@@ -278,7 +278,7 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
-    T = dkm.dkm_last_timings(ctx)   # the last timed step's profiled passes
+    T = dkm.dkm_last_timings(ctx)   # the last timed step's profiled (middle) pass
     a_ms.append(T.assign_ms)
     s_ms.append(T.search_ms)
     u_ms.append(T.update_ms)
@@ -392,7 +392,10 @@ def run_ours(args):
     init = torch.from_numpy(w.init).to(dev)
     C = torch.empty(k * d, dtype=torch.float32, device=dev)
     lab = torch.empty(n, dtype=torch.int32, device=dev)
-    opts = dkm.dkm_default_options(early_stop=0, profile=int(args.profile),
+    # one profiled pass per step (the middle one): the events around its
+    # kernels give the per-kernel times inside the timed region, and a
+    # single profiled pass keeps their cost to the step at about 1%
+    opts = dkm.dkm_default_options(early_stop=0, profile=iters if args.profile else 0,
                                    stream=stream.cuda_stream)
     torch.cuda.synchronize()
     ctx = dkm.dkm_create(pts, n, d, k, opts)
@@ -429,8 +432,8 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     if args.profile:
-        # per-kernel means of the last timed step (CUDA events around the
-        # kernels of every fifth pass, recorded inside the captured graph)
+        # per-kernel times of the last timed step (CUDA events around the
+        # kernels of its middle pass, recorded inside the captured graph)
         T = dkm.dkm_last_timings(ctx)
         assign_ms.append(T.assign_ms)
         search_ms.append(T.search_ms)
@@ -576,7 +579,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", type=int, default=1,
-                    help="record per-kernel CUDA events inside the run graph (roofline)")
+                    help="record per-kernel CUDA events around the middle pass of every "
+                         "timed step, inside the run graph (roofline)")
     ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-brute", action="store_true")

@@ -80,7 +80,10 @@ typedef struct {
     /* dkm_run / dkm_fit: 1 = stop after the first assignment pass that
      * changes no label (default); 0 = always run max_iter passes. */
     int early_stop;
-    /* 1 = record per-kernel CUDA events, read back by dkm_last_timings. */
+    /* Per-kernel CUDA events, read back by dkm_last_timings: 0 = off;
+     * 1 = around the kernels of every fifth pass (every pass of a run of up
+     * to five); n >= 2 = one pass in each n (the middle one of each n).
+     * Each profiled pass costs a run some launch overlap (tens of us). */
     int profile;
     /* cudaStream_t to enqueue on; NULL = legacy default stream. */
     void* stream;
@@ -104,8 +107,7 @@ typedef struct {
     float assign_ms;        /* mean per profiled pass: assignment + accumulation kernel */
     float update_ms;        /* mean per profiled pass: centroid update + grid rebuild */
     float finalize_ms;      /* last dkm_run: label un-permute + final SSE */
-    int passes;             /* profiled passes the means cover: every fifth pass
-                               (every pass of a run of up to five) */
+    int passes;             /* profiled passes the means cover (opts.profile) */
 } dkm_timings;
 
 typedef struct {
@@ -322,9 +324,9 @@ DKM_API dkm_status dkm_query_memory(const dkm_ctx* ctx, size_t* device_bytes, si
 DKM_API dkm_status dkm_get_plan(const dkm_ctx* ctx, dkm_plan_info* out);
 
 /* Timings of the last dkm_setup / dkm_run (needs opts.profile; otherwise
- * 0).  CUDA events are recorded around the kernels of every fifth pass, so
- * profiling adds few graph nodes; the setup time is read out here (this
- * call may wait for the last dkm_setup to finish). */
+ * 0).  CUDA events are recorded around the kernels of the profiled passes
+ * only (opts.profile), so profiling adds few graph nodes; the setup time is
+ * read out here (this call may wait for the last dkm_setup to finish). */
 DKM_API dkm_status dkm_last_timings(dkm_ctx* ctx, dkm_timings* out);
 
 /* Pruning counters of the last pass (reads device counters; synchronises

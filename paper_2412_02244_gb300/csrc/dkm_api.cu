@@ -497,7 +497,15 @@ bool graph_current(const dkm_ctx* c, int iters, int early, int profile) {
 
 // Passes whose kernels get CUDA events when profiling: every fifth pass (all
 // of a run of up to five), so the event nodes stay few in long runs.
-bool profiled_pass(int t, int iters) { return iters <= 5 || t % 5 == 4; }
+// Passes whose kernels are bracketed by CUDA events: one in each `period`
+// (the middle one of each period); with the default period 5 every pass of
+// a run of up to five.  Every event node costs the graph some launch
+// overlap, so long periods keep a timed run close to an unprofiled one.
+int profile_period(const dkm_ctx* c) { return c->opts.profile == 1 ? 5 : c->opts.profile; }
+bool profiled_pass(int t, int iters, int period) {
+  if (period <= 5 && iters <= 5) return true;
+  return t % period == (period - 1) / 2;
+}
 
 dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
   destroy_graph(c);
@@ -523,7 +531,7 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
       A.want_sse = 0;
       // (an early-stopping run may end on any pass: it counts every pass)
       A.want_stats = (early || t + 1 == iters) ? 1 : 0;
-      const bool pe = profile && profiled_pass(t, iters);
+      const bool pe = profile && profiled_pass(t, iters, profile);
       if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, cudaEventRecordExternal))) break;
       if (!brute && (e = launch_search(A, par, c->d, c->stream))) break;
       if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 1], c->stream, cudaEventRecordExternal))) break;
@@ -959,7 +967,7 @@ dkm_status run_impl(dkm_ctx* c, const float* init, int max_iter, float* centroid
   }
   DKM_TRY(ensure_hist(c, max_iter));
   const int early = c->opts.early_stop ? 1 : 0;
-  const int profile = c->opts.profile ? 1 : 0;
+  const int profile = c->opts.profile > 0 ? profile_period(c) : 0;   // 0 or the period
   if (!graph_current(c, max_iter, early, profile))
     DKM_TRY(build_run_graph(c, max_iter, early, profile));
   if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
@@ -981,7 +989,7 @@ dkm_status run_impl(dkm_ctx* c, const float* init, int max_iter, float* centroid
     double s = 0, a = 0, u = 0;
     int p = 0;
     for (int t = 0; t < h->passes && t < max_iter; ++t) {
-      if (!profiled_pass(t, max_iter)) continue;
+      if (!profiled_pass(t, max_iter, profile)) continue;
       s += ev_ms(c->ev[4 * t + 0], c->ev[4 * t + 1]);
       a += ev_ms(c->ev[4 * t + 1], c->ev[4 * t + 2]);
       u += ev_ms(c->ev[4 * t + 2], c->ev[4 * t + 3]);

@@ -357,3 +357,18 @@ def test_exact_ties_survive_pruning(dkm, oracle, d):
     for algo in (dkm.DKM_ALGO_INDEXED, dkm.DKM_ALGO_BRUTE):
         lab_g, _, _ = gpu_assign(dkm, make_ctx(dkm, P, k, algo=algo), C)
         assert np.array_equal(lab_g, lab_o)
+
+
+@pytest.mark.parametrize("profile,expect", [(1, 4), (10, 2), (20, 1)])
+def test_profiled_passes_and_unchanged_results(dkm, profile, expect):
+    """opts.profile sets how many passes carry CUDA events (one in each
+    period, 5 for profile = 1); profiling never changes a result."""
+    w = synth.lidar3d(seed=74, n=40_009, k=60, n_objects=12)
+    plain = gpu_run(dkm, make_ctx(dkm, w.points, w.k, early_stop=0), w.init, 20)
+    ctx = make_ctx(dkm, w.points, w.k, early_stop=0, profile=profile)
+    prof = gpu_run(dkm, ctx, w.init, 20)
+    for x, y in zip(plain, prof):
+        assert np.array_equal(x, y)
+    T = dkm.dkm_last_timings(ctx)
+    assert T.passes == expect
+    assert T.assign_ms > 0 and T.search_ms > 0 and T.iterations_ms > 0
