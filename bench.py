@@ -15,6 +15,7 @@ For N > 1 (torchrun) every rank runs an independent replica (weak scaling).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -62,8 +63,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle samples.  Started before the warm-up (the
+    tool's start-up must not overlap the timed region); summary() keeps the
+    samples taken inside the timed window (the nearest ones if none)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -92,13 +95,13 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, window=None):
         rows = []
         try:
             with open(self.path) as f:
                 for line in f:
                     parts = [x.strip() for x in line.split(",")]
-                    if len(parts) >= 9:
+                    if len(parts) >= 10:
                         rows.append(parts)
         except Exception:
             pass
@@ -107,10 +110,24 @@ class ClockSampler:
                 os.remove(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        if window is not None:
+            def ts(r):
+                try:
+                    return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    return None
+            stamped = [(ts(r), r) for r in rows]
+            inside = [r for t, r in stamped if t is not None and window[0] <= t <= window[1]]
+            if inside:
+                rows = inside
+            else:   # a timed region shorter than the poll interval: the nearest sample
+                mid = 0.5 * (window[0] + window[1])
+                near = [(abs(t - mid), r) for t, r in stamped if t is not None]
+                rows = [min(near, key=lambda x: x[0])[1]] if near else rows
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
@@ -416,21 +433,27 @@ def run_ours(args):
         dkm.dkm_setup(ctx, pts)
         return dkm.dkm_run(ctx, init, iters, C, lab)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     assign_ms, search_ms, update_ms, setup_ms = [], [], [], []
+    # the clock sampler starts before the warm-up: its start-up (NVML
+    # initialisation) would otherwise overlap the timed steps
     with ClockSampler(local) as clk:
+        time.sleep(0.5)
+        for _ in range(args.warmup):
+            step()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
         ev0.record(stream)
         for _ in range(args.steps):
             it, sse = step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        w1 = time.time()
+        time.sleep(0.25)   # let a sample land after the window (for short timed regions)
     if args.profile:
         # per-kernel times of the last timed step (CUDA events around the
         # kernels of its middle pass, recorded inside the captured graph)
@@ -550,7 +573,7 @@ def run_ours(args):
                    "h2d_bytes_per_step": n * d * 4 + k * d * 4,
                    "d2h_bytes_per_step": n * 4 + k * d * 4, "steps": e2e_steps}
     line["gpu_launches"] = launches_per_step(iters) * args.steps
-    line["clocks"] = clk.summary()
+    line["clocks"] = clk.summary(window=(w0, w1))
     if ws == 1 and not args.no_cpu_baseline:
         v, dt, thr = cpu_sample_run(w, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle",
@@ -575,7 +598,7 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", type=int, default=1,

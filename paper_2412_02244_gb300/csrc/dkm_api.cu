@@ -639,7 +639,7 @@ dkm_status plan_clouds(dkm_ctx* c, const std::vector<float>& blo, const std::vec
   return DKM_OK;
 }
 
-dkm_status apply_units(dkm_ctx* c);
+dkm_status apply_units(dkm_ctx* c, bool reset_lists);
 
 // Tiles from the level histogram (device work only, no synchronisation):
 // per cloud the cube level the tiles are cut at (k_choose_levels), then tile
@@ -672,15 +672,19 @@ dkm_status apply_tiling(dkm_ctx* c) {
                          c->stream));
   DKM_CK(cudaStreamSynchronize(c->stream));
   DKM_TRY(finish_tiling(c, *pin_state(c), pin_clouds(c)));
-  return apply_units(c);
+  return apply_units(c, true);
 }
 
 // Search units (hierarchical tiles): groups of unit_g consecutive tiles of
 // one cloud share one grid search over the union of their boxes, and each
 // tile narrows the unit's list with its own box in k_assign.  unit_g = 1:
 // every tile is its own unit.
-dkm_status apply_units(dkm_ctx* c) {
-  DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
+// Candidate lists only seed the next search's bound (k_search ignores ids
+// outside the tile's cloud), so they survive a rebuild of the same tiling
+// (dkm_setup) and are cleared when the tiles or units are re-cut
+// (reset_lists).  The stay test's single labels always are.
+dkm_status apply_units(dkm_ctx* c, bool reset_lists) {
+  if (reset_lists) DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
   DKM_CK(cudaMemsetAsync(c->tlab, 0xff, sizeof(int) * c->tiles_cap, c->stream));
   if (c->unit_g <= 1) {
     c->n_units = c->n_tiles;
@@ -773,7 +777,8 @@ dkm_status setup_impl(dkm_ctx* c, const float* points) {
   DKM_TRY(finish_tiling(c, h, pin_clouds(c)));
   DKM_TRY(plan_clouds(c, c->h_blo, c->h_bhi));
   DKM_TRY(upload_clouds(c));
-  DKM_TRY(apply_units(c));
+  DKM_TRY(apply_units(c, !c->lists_seeded));   // lists of an earlier setup stay as seeds
+  c->lists_seeded = true;
   if (c->opts.profile) {   // read out lazily (dkm_last_timings), no synchronisation here
     DKM_CK(cudaEventRecord(c->ev_s, c->stream));
     c->setup_pending = true;
@@ -1065,7 +1070,7 @@ dkm_status apply_tuning(dkm_ctx* c, const dkm_tuning& t) {
   }
   if (t.tile_group != c->unit_g) {
     c->unit_g = t.tile_group;
-    DKM_TRY(apply_units(c));
+    DKM_TRY(apply_units(c, true));
     changed = true;
   }
   if (changed) {

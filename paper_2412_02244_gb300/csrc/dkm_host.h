@@ -96,6 +96,7 @@ struct dkm_ctx {
   int sort_max = 0;            // sorted early-exit evaluation for lists up to this length
   int stay = 0;                // the bound layer's stay test (tile_group 1 only)
   bool ready = false;          // the point index is valid
+  bool lists_seeded = false;   // the candidate-list counters were cleared once
   bool acc_valid = false;      // acc holds the sums of the last dkm_assign
 
   // device arena

@@ -300,9 +300,9 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   // ---- phase A ----
   // Any centroid of the cloud bounds the nearest distance of every point in
   // the box by maxd(box, c).  The tile's list of the previous pass holds
-  // ids of this cloud near the tile (lists are cleared whenever the tiles
-  // change), so its current positions give U in one load round; without a
-  // list, rings of cells around the box are scanned.
+  // ids near the tile, so its current positions give U in one load round;
+  // ids outside the cloud (a list left by another tiling) are skipped.
+  // Without a usable list, rings of cells around the box are scanned.
   // The centroid that gives U (r1) also serves as the dominance reference
   // of phase B.
   float u2 = INFINITY;
@@ -311,7 +311,9 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   const int q_old = A.tcnt[t];
   if (q_old >= 1 && q_old <= kTileCap) {
     for (int j = lane; j < q_old; j += 32) {
-      const float4 c = A.cw[__float_as_int(out[j].w)];
+      const int id = __float_as_int(out[j].w);
+      if (id < c0 || id >= c1) continue;
+      const float4 c = A.cw[id];
       const float mc = maxd2(lo, hi, c.x, c.y, c.z, d);
       if (mc < m) { m = mc; r1 = c; }
     }
