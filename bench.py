@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "f5e7fd7df4a08f3a", "bytes_per_launch": 129_725_952 + 22_583_296,
+NCU_TRAFFIC = {"sha": "6646a5afc6f4a134", "bytes_per_launch": 129_772_800 + 23_162_880,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
