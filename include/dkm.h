@@ -82,8 +82,9 @@ typedef struct {
     int early_stop;
     /* Per-kernel CUDA events, read back by dkm_last_timings: 0 = off;
      * 1 = around the kernels of every fifth pass (every pass of a run of up
-     * to five); n >= 2 = one pass in each n (the middle one of each n).
-     * Each profiled pass costs a run some launch overlap (tens of us). */
+     * to five); n >= 2 = one pass in each n (the middle one of each n; the
+     * middle pass of a run shorter than n).  Each profiled pass costs a run
+     * some launch overlap (tens of us). */
     int profile;
     /* cudaStream_t to enqueue on; NULL = legacy default stream. */
     void* stream;

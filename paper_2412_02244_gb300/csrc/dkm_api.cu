@@ -498,12 +498,14 @@ bool graph_current(const dkm_ctx* c, int iters, int early, int profile) {
 // Passes whose kernels get CUDA events when profiling: every fifth pass (all
 // of a run of up to five), so the event nodes stay few in long runs.
 // Passes whose kernels are bracketed by CUDA events: one in each `period`
-// (the middle one of each period); with the default period 5 every pass of
-// a run of up to five.  Every event node costs the graph some launch
-// overlap, so long periods keep a timed run close to an unprofiled one.
+// (the middle one of each period), the middle pass of a run shorter than
+// the period, and with the default period 5 every pass of a run of up to
+// five.  Every event node costs the graph some launch overlap, so long
+// periods keep a timed run close to an unprofiled one.
 int profile_period(const dkm_ctx* c) { return c->opts.profile == 1 ? 5 : c->opts.profile; }
 bool profiled_pass(int t, int iters, int period) {
   if (period <= 5 && iters <= 5) return true;
+  if (iters < period) return t == (iters - 1) / 2;
   return t % period == (period - 1) / 2;
 }
 

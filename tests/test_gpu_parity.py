@@ -359,7 +359,7 @@ def test_exact_ties_survive_pruning(dkm, oracle, d):
         assert np.array_equal(lab_g, lab_o)
 
 
-@pytest.mark.parametrize("profile,expect", [(1, 4), (10, 2), (20, 1)])
+@pytest.mark.parametrize("profile,expect", [(1, 4), (10, 2), (20, 1), (50, 1)])
 def test_profiled_passes_and_unchanged_results(dkm, profile, expect):
     """opts.profile sets how many passes carry CUDA events (one in each
     period, 5 for profile = 1); profiling never changes a result."""
