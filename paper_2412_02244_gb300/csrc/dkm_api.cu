@@ -495,8 +495,6 @@ bool graph_current(const dkm_ctx* c, int iters, int early, int profile) {
   return memcmp(&now, &c->g_args, sizeof(IterArgs)) == 0;
 }
 
-// Passes whose kernels get CUDA events when profiling: every fifth pass (all
-// of a run of up to five), so the event nodes stay few in long runs.
 // Passes whose kernels are bracketed by CUDA events: one in each `period`
 // (the middle one of each period), the middle pass of a run shorter than
 // the period, and with the default period 5 every pass of a run of up to
