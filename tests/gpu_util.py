@@ -67,3 +67,57 @@ def check_labels(lab_g, lab_o, best, second):
         f"{int(bad.sum())} labels differ; {int((gap >= LABEL_GAP).sum())} of them are not "
         f"near-ties (max gap {gap.max():.3g})")
     return int(bad.sum())
+
+
+def replay_free_running(dkm, oracle, pts, k, init, max_iter, early_stop, **opts):
+    """A free-running dkm_run checked against the FP64 oracle pass by pass.
+
+    dkm_run equals the composition of dkm_assign + dkm_update(NULL) bit for
+    bit, so the run's trajectory is replayed one pass at a time on a second
+    context, and every pass is checked against the oracle at the GPU's own
+    centroids: labels equal except near-ties (Eq. 1 argmin), the update of
+    those labels within the centroid tolerance (Algorithm 1 refine step).
+    The run's final labels and centroids must equal the replay's bit for
+    bit.  Then the run is compared with an independent oracle.fit, whose
+    centroids stay in FP64 from pass to pass while the GPU's are rounded to
+    FP32 (the caller's type): the two trajectories differ by that rounding,
+    which near the end of a long run moves more labels than the near-tie
+    band of one pass covers (coordinates near 1e5 have an FP32 ulp of
+    0.008).  So the final SSE must agree within 1e-4; when the final labels
+    agree too, so must the pass count and the centroids.
+    Returns (near-tie flips seen, fraction of final labels equal to the
+    oracle fit's)."""
+    ext = extent(pts)
+    ctx = make_ctx(dkm, pts, k, early_stop=early_stop, **opts)
+    C_r, lab_r, it_r, sse_r = gpu_run(dkm, ctx, init, max_iter)
+    ctx.close()
+    ctx2 = make_ctx(dkm, pts, k, early_stop=early_stop, **opts)
+    C = np.asarray(init, np.float32).copy()
+    flips = 0
+    lab = chg = None
+    for t in range(it_r):
+        lab, sse, chg = gpu_assign(dkm, ctx2, C)
+        C64 = C.astype(np.float64)
+        lab_o, best, second = oracle.assign(pts, C64)
+        flips += check_labels(lab, lab_o, best, second)
+        assert abs(sse - best.sum()) <= SSE_RTOL * best.sum(), f"pass {t}: SSE"
+        C_next, cnt = gpu_update(dkm, ctx2, None, C)
+        C_o, cnt_o = oracle.update(pts, lab, C64)
+        assert np.array_equal(cnt, cnt_o), f"pass {t}: cluster sizes"
+        err = np.abs(C_next.astype(np.float64) - C_o).max()
+        assert err <= CENTROID_TOL * ext, f"pass {t}: centroid error {err:.3g}"
+        C = C_next
+    ctx2.close()
+    assert np.array_equal(C, C_r), "dkm_run's centroids differ from its pass-by-pass replay"
+    if it_r > 0:
+        assert np.array_equal(lab, lab_r), "dkm_run's labels differ from its replay"
+    if early_stop and it_r < max_iter:
+        assert chg == 0, "an early-stopped run must end on a pass that changed no label"
+    r = oracle.fit(pts, np.asarray(init, np.float64), max_iter, early_stop=bool(early_stop))
+    assert abs(sse_r - oracle.sse(pts, lab_r, C_r.astype(np.float64))) <= SSE_RTOL * sse_r
+    assert abs(sse_r - r["sse"]) <= SSE_RTOL * r["sse"]
+    agree = float(np.mean(lab_r == r["labels"])) if it_r > 0 else 1.0
+    if agree == 1.0:
+        assert it_r == r["iterations"]
+        assert np.abs(C_r.astype(np.float64) - r["centroids"]).max() <= CENTROID_TOL * ext
+    return flips, agree

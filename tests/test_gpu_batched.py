@@ -206,11 +206,15 @@ def test_batched_uneven_workload_full_size(dkm, oracle):
                                      dict(tile_group=4), dict(tile_group=32),
                                      dict(tile_group=8, sort_max=32), dict(stay_test=1),
                                      dict(stay_test=1, sort_max=32)])
-def test_tuning_settings_keep_labels_exact(dkm, setting):
-    """Every index setting labels exactly like brute force.  The SSE is a sum
-    of per-tile fixed-point partials (each tile at its own power-of-two
-    scale), so a setting that regroups the tiles moves its last bits: it is
-    compared to 1e-6 relative, the labels bit for bit."""
+def test_tuning_settings_keep_labels_exact(dkm, oracle, setting):
+    """Every index setting labels exactly like brute force, and cloud by
+    cloud like the FP64 oracle (near-ties aside); the setting's own update
+    sums match the oracle's update of those labels.  The SSE is a sum of
+    per-tile fixed-point partials (each tile at its own power-of-two scale),
+    so a setting that regroups the tiles moves its last bits: it is compared
+    to 1e-6 relative, the labels bit for bit.  Lock-step: both sides continue
+    from the oracle's centroids; six passes, so that the bound layer's stay
+    test (Section IV-A) has tiles to keep."""
     P, off, ks, coff, init = _small(3, seed=51)
     ctx = _ctx(dkm, P, off, ks)
     ctx_b = _ctx(dkm, P, off, ks, algo=dkm.DKM_ALGO_BRUTE)
@@ -219,12 +223,29 @@ def test_tuning_settings_keep_labels_exact(dkm, setting):
     for k, v in setting.items():
         assert getattr(t, k) == pytest.approx(v)
     C = init.copy()
-    for _ in range(3):
+    flips = 0
+    stays = 0
+    for _ in range(6):
         lab, sse, _ = gpu_assign(dkm, ctx, C)
         lab_b, sse_b, _ = gpu_assign(dkm, ctx_b, C)
         assert np.array_equal(lab, lab_b)
         assert abs(sse - sse_b) <= 1e-6 * sse_b
-        C, _ = gpu_update(dkm, ctx_b, lab_b, C)
+        stays += dkm.dkm_last_stats(ctx).stayed_tiles
+        C_g, _ = gpu_update(dkm, ctx, None, C)
+        C_next = np.empty_like(C)
+        for b in range(len(ks)):
+            ps, cs = slice(off[b], off[b + 1]), slice(coff[b], coff[b + 1])
+            Pb, Cb = P[ps], C[cs].astype(np.float64)
+            lo, best, second = oracle.assign(Pb, Cb)
+            flips += check_labels(lab[ps], lo, best, second)
+            C_o, _ = oracle.update(Pb, lab[ps], Cb)
+            err = np.abs(C_g[cs].astype(np.float64) - C_o).max()
+            assert err <= CENTROID_TOL * extent(Pb), f"cloud {b}: centroid error {err:.3g}"
+            C_next[cs] = C_o.astype(np.float32)
+        C = C_next
+    assert flips <= 2
+    if setting.get("stay_test"):
+        assert stays > 0
 
 
 def test_autotune_choice_cache_and_exactness(dkm):
@@ -264,7 +285,7 @@ def test_tuning_rejects_bad_values(dkm):
 
 
 @pytest.mark.parametrize("batched", [False, True])
-def test_stay_test_gives_the_same_run_bit_for_bit(dkm, batched):
+def test_stay_test_gives_the_same_run_bit_for_bit(dkm, oracle, batched):
     """The bound layer only skips searches whose outcome it has proved, so a
     run with it equals the run without it in every bit, and near
     convergence some tiles do stay."""
@@ -287,3 +308,23 @@ def test_stay_test_gives_the_same_run_bit_for_bit(dkm, batched):
     (C0, l0, i0, s0), (C1, l1, i1, s1) = out
     assert np.array_equal(C0, C1) and np.array_equal(l0, l1)
     assert np.array_equal(i0, i1) and np.array_equal(s0, s1)
+    # and the bound layer keeps Lloyd's result: after the same run, one more
+    # pass with the stay test from the run's final centroids labels every
+    # cloud like the oracle (near-ties aside) and updates like the oracle
+    ctx = _ctx(dkm, P, off, ks, early_stop=0)
+    dkm.dkm_set_tuning(ctx, stay_test=1)
+    _run(dkm, ctx, init, 12)
+    lab, _, _ = gpu_assign(dkm, ctx, C1)
+    C_g, _ = gpu_update(dkm, ctx, None, C1)
+    coff = np.zeros(len(ks) + 1, np.int64)
+    coff[1:] = np.cumsum(ks)
+    flips = 0
+    for b in range(len(ks)):
+        ps, cs = slice(off[b], off[b + 1]), slice(coff[b], coff[b + 1])
+        Pb, Cb = P[ps], C1[cs].astype(np.float64)
+        lo, best, second = oracle.assign(Pb, Cb)
+        flips += check_labels(lab[ps], lo, best, second)
+        C_o, _ = oracle.update(Pb, lab[ps], Cb)
+        assert np.abs(C_g[cs].astype(np.float64) - C_o).max() <= CENTROID_TOL * extent(Pb)
+    assert flips <= 2
+    assert dkm.dkm_last_stats(ctx).stayed_tiles > 0
