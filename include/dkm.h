@@ -352,7 +352,8 @@ DKM_API void dkm_destroy(dkm_ctx* ctx);
  * Soft k-means with T unrolled steps at a fixed temperature tau[b]:
  *   w^t_ij = softmax_j(-||p_i - c^t_j||^2 / tau),
  *   c^{t+1}_j = sum_i w^t_ij p_i / sum_i w^t_ij   (a centroid whose weights
- *     all underflow to zero in FP32 keeps its position),
+ *     all underflow to zero in FP32 keeps its position, and the backward
+ *     passes the gradient of c^{t+1}_j on to c^t_j unchanged),
  *   loss[b] = sum_ij w^T_ij ||p_i - c^T_j||^2.
  * dkm_soft_forward writes the centroids of every step into ckpt
  * (B x (T+1) x k x d, step-major: ckpt[t] is B x k x d) and the loss.
@@ -389,6 +390,33 @@ DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int
                                 const float* centroids, int32_t* labels, double* loss,
                                 float* grad_points, float* grad_centroids, void* stream);
 
+/*
+ * Backward of the hard SSE for an upstream gradient dloss[b] = dOut/dloss[b]
+ * (B doubles, host or device): given the labels the forward returned
+ * (n_total int32, cloud-local, device), writes
+ *   grad_points[i]     = dloss[b] * 2 (p_i - c_a(i)),
+ *   grad_centroids[j]  = dloss[b] * -2 sum_{a(i)=j} (p_i - c_j),
+ * either of them nullable.  Same layout and pointer rules as
+ * dkm_soft_forward.  Errors: DKM_EINVAL (sizes, null pointers, a label
+ * outside [0, k): the gradient rows of such points are 0), DKM_ECUDA.
+ */
+DKM_API dkm_status dkm_hard_sse_backward(const float* points, const int64_t* offsets, int B,
+                                         int d, int k, const float* centroids,
+                                         const int32_t* labels, const double* dloss,
+                                         float* grad_points, float* grad_centroids,
+                                         void* stream);
+
+/*
+ * Temperature of the soft loss per cloud: tau[b] = frac * ||hi_b - lo_b||^2,
+ * the squared diagonal of cloud b's bounding box (FP32 box corners, FP64
+ * sum of squares, rounded to FP32).  The default of the differentiable
+ * workload is frac = 0.01.  points (device), offsets and tau (B floats)
+ * host or device.  Errors: DKM_EINVAL (sizes, offsets, null pointers,
+ * frac <= 0), DKM_ECUDA.
+ */
+DKM_API dkm_status dkm_soft_temperature(const float* points, const int64_t* offsets, int B, int d,
+                                        double frac, float* tau, void* stream);
+
 /* Largest k dkm_lloyd_step_noalloc accepts (its fixed scratch holds k
  * cluster accumulators of 32 bytes each, about 2 MiB in all). */
 #define DKM_NOALLOC_MAX_K 65536
@@ -417,13 +445,41 @@ DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int
  * device (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Each call clears what must start at zero.  All calls share the
  * one array, so calls that overlap on the GPU (other streams, other host
- * threads) race; serialise them.  Inputs are not checked for NaN/Inf.
+ * threads) race; serialise them.
+ * A NaN or infinite coordinate in points or centroids is detected on the
+ * GPU: every label is then set to -1, centroids_out receives centroids
+ * unchanged, and the SSE is NaN.  With sse_out the call reads that result
+ * back and returns DKM_EINVAL; without it the call returns before the GPU
+ * has looked at the data, so the caller must check the labels.
  * Errors: DKM_EINVAL (d not 2/3, n < 1, k < 1 or k > DKM_NOALLOC_MAX_K,
- * null pointer) before any GPU work; DKM_ECUDA.
+ * null pointer) before any GPU work, or non-finite input (with sse_out);
+ * DKM_ECUDA.
  */
 DKM_API dkm_status dkm_lloyd_step_noalloc(const float* points, int64_t n, int d, int k,
                                           const float* centroids, float* centroids_out,
                                           int32_t* labels, double* sse_out, void* stream);
+
+/*
+ * Device peaks for roofline reporting (no counterpart in the paper).  The
+ * brute-force assignment and the soft k-means passes are bound by FP32
+ * arithmetic, not by memory; their achieved rate is reported against the
+ * FP32 FMA throughput measured here: FMA-chain kernels (eight independent
+ * chains per thread, eight 256-thread CTAs per SM), scalar fmaf and packed
+ * f32x2, each timed with CUDA events after a warm-up launch.  An FMA counts
+ * as two floating-point operations.  Runs on the current device and
+ * stream (NULL = legacy default); allocates a small output buffer with the
+ * stream-ordered allocator.  Errors: DKM_EINVAL (null out), DKM_ECUDA.
+ */
+typedef struct {
+    int sm_count;               /* multiprocessors of the current device */
+    int sm_clock_mhz;           /* its rated maximum SM clock */
+    double fp32_fma_tflops;     /* measured, scalar FFMA */
+    double fp32x2_fma_tflops;   /* measured, packed f32x2 FFMA */
+    float scalar_ms;            /* duration of the timed scalar launch */
+    float packed_ms;            /* duration of the timed packed launch */
+} dkm_peaks;
+
+DKM_API dkm_status dkm_device_peaks(dkm_peaks* out, void* stream);
 
 /*
  * Self-test of the library's one device-side wait: the radix sort of
@@ -431,6 +487,9 @@ DKM_API dkm_status dkm_lloyd_step_noalloc(const float* points, int64_t n, int d,
  * the CTAs before them.  Runs one sort pass on 8,192 keys whose only CTA
  * is handed the second tile, so the count it waits for is never published:
  * the wait must give up by itself (after about a second) and report it.
+ * The points are then gathered by the partly written order, as dkm_setup
+ * does before it reads the error flag; the slots the pass never wrote hold
+ * out-of-range indices, which the gather must clamp.
  * Allocates and frees its own small device buffers on a private stream.
  * seconds_out (nullable, host): the wall time of the pass.
  * Returns DKM_OK if the wait ended and was reported; DKM_EINTERNAL if the

@@ -1,14 +1,15 @@
 """torch.autograd.Function wrappers of the differentiable k-means losses.
 
 Both run entirely in libdkm's kernels (dkm_soft_forward / dkm_soft_backward
-/ dkm_hard_sse); this module only allocates the output tensors and routes
-the upstream gradient.
+/ dkm_hard_sse / dkm_hard_sse_backward / dkm_soft_temperature); this module
+only allocates the output tensors and routes the upstream gradient.
 
   SoftKMeansLoss.apply(points, init, offsets, tau, T) -> loss (B,) float64
       points  (n_total, d) float32 CUDA, clouds concatenated
       init    (B, k, d)    float32 CUDA, initial centroids
       offsets (B + 1,)     int64 (CPU), cloud b = points[offsets[b]:offsets[b+1]]
-      tau     (B,)         float32 (CPU), temperature per cloud (a constant)
+      tau     (B,)         float32 (CPU), temperature per cloud (a constant);
+                           None = temperature(points, offsets)
       T       int          unrolled soft k-means steps
     Gradients flow to points and init.
 
@@ -27,14 +28,14 @@ def _stream() -> int:
 
 
 def temperature(points: torch.Tensor, offsets: torch.Tensor, frac: float = 0.01) -> torch.Tensor:
-    """tau_b = frac x squared bounding-box diagonal of cloud b (CPU float32)."""
-    out = []
-    off = offsets.tolist()
-    for b in range(len(off) - 1):
-        P = points[off[b]:off[b + 1]]
-        ext = P.max(dim=0).values - P.min(dim=0).values
-        out.append(frac * float((ext.double() ** 2).sum()))
-    return torch.tensor(out, dtype=torch.float32)
+    """tau_b = frac x squared bounding-box diagonal of cloud b (CPU float32),
+    computed on the GPU by dkm_soft_temperature."""
+    offsets = offsets.to(torch.int64).cpu().contiguous()
+    B = offsets.numel() - 1
+    tau = torch.empty(B, dtype=torch.float32)
+    dkm.dkm_soft_temperature(points.contiguous(), offsets, B, points.shape[1], tau, frac,
+                             _stream())
+    return tau
 
 
 class SoftKMeansLoss(torch.autograd.Function):
@@ -44,6 +45,8 @@ class SoftKMeansLoss(torch.autograd.Function):
         points = points.contiguous()
         init = init.contiguous()
         offsets = offsets.to(torch.int64).cpu().contiguous()
+        if tau is None:
+            tau = temperature(points, offsets)
         tau = tau.to(torch.float32).cpu().contiguous()
         ckpt = torch.empty((T + 1, B, k, d), dtype=torch.float32, device=points.device)
         loss = torch.empty(B, dtype=torch.float64, device=points.device)
@@ -78,16 +81,19 @@ class HardSSELoss(torch.autograd.Function):
         centroids = centroids.contiguous()
         offsets = offsets.to(torch.int64).cpu().contiguous()
         loss = torch.empty(B, dtype=torch.float64, device=points.device)
-        gp = torch.empty_like(points)
-        gc = torch.empty_like(centroids)
-        dkm.dkm_hard_sse(points, offsets, B, d, k, centroids, None, loss, gp, gc, _stream())
-        ctx.save_for_backward(gp, gc)
+        labels = torch.empty(points.shape[0], dtype=torch.int32, device=points.device)
+        dkm.dkm_hard_sse(points, offsets, B, d, k, centroids, labels, loss, None, None, _stream())
+        ctx.save_for_backward(points, centroids, labels)
         ctx.offsets = offsets
         return loss
 
     @staticmethod
     def backward(ctx, gloss):
-        gp, gc = ctx.saved_tensors
-        sizes = (ctx.offsets[1:] - ctx.offsets[:-1]).to(gp.device)
-        w = gloss.to(torch.float32)
-        return gp * torch.repeat_interleave(w, sizes)[:, None], gc * w[:, None, None], None
+        points, centroids, labels = ctx.saved_tensors
+        B, k, d = centroids.shape
+        gp = torch.empty_like(points) if ctx.needs_input_grad[0] else None
+        gc = torch.empty_like(centroids) if ctx.needs_input_grad[1] else None
+        dl = gloss.detach().to(torch.float64).contiguous()
+        dkm.dkm_hard_sse_backward(points, ctx.offsets, B, d, k, centroids, labels, dl, gp, gc,
+                                  _stream())
+        return gp, gc, None

@@ -296,15 +296,6 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   return A;
 }
 
-// Tuning knob, read once per context: DKM_ROW_FILTER_MIN (default 48).
-int env_int(const char* name, int def) {
-  const char* v = getenv(name);
-  if (!v || !*v) return def;
-  char* end = nullptr;
-  long x = strtol(v, &end, 10);
-  return (end && *end == 0) ? (int)x : def;
-}
-
 dkm_status check_ctx(const dkm_ctx* c) {
   if (!c) return fail(DKM_EINVAL, "null context");
   if (!c->ready) return fail(DKM_EINVAL, "context has no valid point index (a dkm_setup failed)");
@@ -810,7 +801,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->k = (int)c->coffs[c->B];
   c->opts = resolve(opts);
   c->cpc = c->opts.cells_per_centroid;
-  c->row_filter_min = env_int("DKM_ROW_FILTER_MIN", 48);
+  c->row_filter_min = 48;   // default tuning (dkm_set_tuning changes it)
   // sort key: cloud index in the top cb bits, mb Morton bits per axis below
   int cb = 0;
   while ((1 << cb) < c->B) ++cb;
@@ -1263,7 +1254,10 @@ dkm_status dkm_selftest_wait(double* seconds_out) {
   void* buf = nullptr;
   const size_t key_bytes = sizeof(uint32_t) * n;
   const size_t scratch = rs_scratch_bytes(n);
-  const size_t total = 4 * key_bytes + scratch + sizeof(DevState);
+  // after the pass: the n x 3 points the gather reads and its SoA output
+  const size_t pts_bytes = sizeof(float) * 3 * n;
+  const size_t soa_bytes = sizeof(float) * 3 * n;
+  const size_t total = 4 * key_bytes + scratch + sizeof(DevState) + pts_bytes + soa_bytes;
   cudaStream_t s = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
     return fail(DKM_ECUDA, "cudaStreamCreate failed");
@@ -1276,12 +1270,21 @@ dkm_status dkm_selftest_wait(double* seconds_out) {
   uint32_t* vals[2] = {(uint32_t*)(base + 2 * key_bytes), (uint32_t*)(base + 3 * key_bytes)};
   void* scr = base + 4 * key_bytes;
   DevState* st = (DevState*)(base + 4 * key_bytes + scratch);   // scratch is a multiple of 8
+  float* pts = (float*)(base + 4 * key_bytes + scratch + sizeof(DevState));
+  float* soa = pts + 3 * n;
   dkm_status r = DKM_OK;
   const auto t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaMemsetAsync(buf, 0, total, s);
+  // the pass's value output starts as out-of-range indices, so every slot
+  // the interrupted pass leaves unwritten is a stale entry
+  if (e == cudaSuccess) e = cudaMemsetAsync(vals[1], 0xff, key_bytes, s);
   if (e == cudaSuccess) e = launch_sort_wait_selftest(keys, vals, n, scr, st, s);
   const double sec =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // dkm_setup gathers the points by the sort's order before it reads the
+  // error flag: that gather must stay inside the point array too
+  if (e == cudaSuccess) e = launch_gather(pts, n, 3, vals[1], soa, soa + n, soa + 2 * n, n, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   int flag = 0;
   if (e == cudaSuccess)
     e = cudaMemcpy(&flag, &st->sort_err, sizeof(int), cudaMemcpyDeviceToHost);

@@ -24,11 +24,18 @@ constexpr int kNaMaxK = DKM_NOALLOC_MAX_K;
 constexpr int kNaSlots = 256;
 constexpr int kNaChunk = 1024;   // centroids staged in shared memory per round
 
+// What the host reads back after a step (one copy).
+struct NaResult {
+  double sse;   // SSE of the labels against the input centroids (NaN if bad)
+  int bad;      // a point or centroid coordinate was NaN or infinite
+  int pad;
+};
+
 struct NaScratch {
   Acc acc[kNaMaxK];                  // per-cluster residual sums (fixed point) + counts
   unsigned long long sse[kNaSlots];  // spread SSE counters (fixed point)
   DevState st;                       // bounding boxes for the fixed-point scale
-  double sse_total;
+  NaResult res;
 };
 
 // Every GPU that loads the library holds this array until the process
@@ -40,6 +47,7 @@ __global__ void k_na_clear(NaScratch* s, int k, int d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < k) s->acc[i] = Acc{{0ull, 0ull, 0ull}, 0ull};
   if (i < kNaSlots) s->sse[i] = 0ull;
+  if (i == 0) s->res.bad = 0;
   if (i < 3) {
     unsigned lo = i < d ? 0xffffffffu : ord_of(0.f), hi = i < d ? 0u : ord_of(0.f);
     s->st.pbox[i] = lo;
@@ -49,16 +57,20 @@ __global__ void k_na_clear(NaScratch* s, int k, int d) {
   }
 }
 
-// bounding box of an m x d array into pbox (which = 0) or cbox (which = 1)
+// bounding box of an m x d array into pbox (which = 0) or cbox (which = 1);
+// a NaN or infinite coordinate sets res.bad
 __global__ void k_na_bbox(const float* __restrict__ p, int64_t m, int d, NaScratch* s, int which) {
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
     for (int a = 0; a < d; ++a) {
       const float v = p[i * d + a];
+      bad = bad || !isfinite(v);
       lo[a] = fminf(lo[a], v);
       hi[a] = fmaxf(hi[a], v);
     }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&s->res.bad, 1);
   for (int a = 0; a < 3; ++a)
     for (int o = 16; o > 0; o >>= 1) {
       lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
@@ -86,6 +98,10 @@ __global__ void __launch_bounds__(256) k_na_assign(const float* __restrict__ pts
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool v = i < n;
+  if (s->res.bad) {   // non-finite input (the same flag for every thread): no labels
+    if (v) labels[i] = -1;
+    return;
+  }
   float px = 0.f, py = 0.f, pz = 0.f;
   if (v) {
     px = pts[i * D + 0];
@@ -163,14 +179,20 @@ __global__ void __launch_bounds__(256) k_na_assign(const float* __restrict__ pts
 __global__ void k_na_update(const float* __restrict__ C, int k, int d, int64_t n,
                             float* __restrict__ out, NaScratch* s) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool bad = s->res.bad != 0;
   if (j == 0) {
     int s_glob, s_sse;
     fixed_exponents(&s->st, n, &s_glob, &s_sse);
     unsigned long long t = 0;
     for (int q = 0; q < kNaSlots; ++q) t += s->sse[q];
-    s->sse_total = (double)(long long)t * exp2(-(double)s_sse);
+    s->res.sse = bad ? __longlong_as_double(0x7ff8000000000000ll)
+                     : (double)(long long)t * exp2(-(double)s_sse);
   }
   if (j >= k) return;
+  if (bad) {   // non-finite input: the centroids pass through unchanged
+    for (int t = 0; t < d; ++t) out[(int64_t)j * d + t] = C[(int64_t)j * d + t];
+    return;
+  }
   const Acc a = s->acc[j];
   const long long cnt = (long long)a.cnt;
   int s_glob, s_sse;
@@ -247,9 +269,14 @@ extern "C" DKM_API dkm_status dkm_lloyd_step_noalloc(const float* points, int64_
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(DKM_ECUDA, "dkm_lloyd_step_noalloc: launch failed", e);
   if (sse_out) {
-    e = cudaMemcpyAsync(sse_out, &s->sse_total, sizeof(double), cudaMemcpyDeviceToHost, st);
+    NaResult res;
+    e = cudaMemcpyAsync(&res, &s->res, sizeof(NaResult), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return na_fail(DKM_ECUDA, "dkm_lloyd_step_noalloc: SSE read-back", e);
+    *sse_out = res.sse;
+    if (res.bad)
+      return na_fail(DKM_EINVAL, "dkm_lloyd_step_noalloc: a point or centroid coordinate is NaN "
+                                 "or infinite (labels set to -1, centroids copied through)");
   }
   return DKM_OK;
 }

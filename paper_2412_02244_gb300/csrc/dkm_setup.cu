@@ -484,8 +484,12 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ p, int
                                                 float* __restrict__ zs, int64_t n_pad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
-  // padding slots (i >= n) repeat the last sorted point; they are never labelled
-  int64_t src = order[i < n ? i : n - 1];
+  // padding slots (i >= n) repeat the last sorted point; they are never labelled.
+  // A sort whose look-back gave up (sort_err) can leave stale entries in
+  // `order`; the clamp keeps every read inside the point array (the setup
+  // then reports DKM_ETIMEOUT).
+  const uint32_t o = order[i < n ? i : n - 1];
+  const int64_t src = (int64_t)o < n ? (int64_t)o : n - 1;
   xs[i] = p[src * d + 0];
   ys[i] = p[src * d + 1];
   if (d == 3) zs[i] = p[src * d + 2];
@@ -508,8 +512,9 @@ __device__ __forceinline__ int first_diff_level(uint32_t a, uint32_t b, int d, i
   return mb - p / d;                       // 1 = the coarsest level
 }
 
+// (clamped: keys left stale by a sort that gave up still index in bounds)
 __device__ __forceinline__ int cloud_of_key(uint32_t key, int d, int mb, int B) {
-  return B > 1 ? (int)(key >> (d * mb)) : 0;
+  return B > 1 ? min((int)(key >> (d * mb)), B - 1) : 0;
 }
 
 // hist: B x (kMaxLevels + 1) counters.  With smem_hist the CTA first

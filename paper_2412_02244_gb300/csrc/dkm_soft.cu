@@ -20,6 +20,7 @@
 // run in FP32 over chunks of 64 points and in FP64 across chunks; splits
 // are combined in a fixed order, so results are deterministic.
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -43,9 +44,12 @@ struct SoftArgs {
   float* aux;             // per point: rho_i (soft step) or E_i (loss stage)
   double* part;           // B x ns x k x 4 column partials
   int use_stats;          // kRowStep: m and iz given (from the forward), not recomputed
+  int* bad;               // set when a given label lies outside [0, k)
 };
 
-enum RowMode { kRowStats = 0, kRowLoss = 1, kRowStep = 2, kRowLossBwd = 3, kRowHard = 4 };
+enum RowMode {
+  kRowStats = 0, kRowLoss = 1, kRowStep = 2, kRowLossBwd = 3, kRowHard = 4, kRowHardBwd = 5
+};
 enum ColMode { kColMean = 0, kColStep = 1, kColLoss = 2, kColHard = 3 };
 
 template <int D>
@@ -102,7 +106,23 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
   const float it = 1.f / A.tau[b];
   double contrib = 0.0;
   float3 dv;
-  if (MODE == kRowHard) {
+  if (MODE == kRowHardBwd) {
+    // dOut/dp_i = dloss[b] * 2 (p_i - c_a(i)), a(i) the forward's label
+    if (valid) {
+      const int a = labels[i];
+      if (a < 0 || a >= k) {
+        atomicOr(A.bad, 1);
+        gP[i * D + 0] = gP[i * D + 1] = 0.f;
+        if (D == 3) gP[i * D + 2] = 0.f;
+      } else {
+        sqd<D>(p, sc[a], dv);
+        const float s2 = 2.f * (float)dloss[b];
+        gP[i * D + 0] = s2 * dv.x;
+        gP[i * D + 1] = s2 * dv.y;
+        if (D == 3) gP[i * D + 2] = s2 * dv.z;
+      }
+    }
+  } else if (MODE == kRowHard) {
     float best = INFINITY;
     int a = 0;
     for (int j = 0; j < k; ++j) {
@@ -259,7 +279,9 @@ __global__ void k_soft_col(SoftArgs A, const float* __restrict__ Ct, const float
         const float3 p = make_float3(pq.x, pq.y, pq.z);
         float3 dv;
         if (MODE == kColHard) {
-          if (__float_as_int(aq.z) == j) {
+          const int lq = __float_as_int(aq.z);
+          if (j == 0 && (lq < 0 || lq >= k)) atomicOr(A.bad, 1);
+          if (lq == j) {
             sqd<D>(p, c, dv);
             f[0] += dv.x; f[1] += dv.y; f[2] += dv.z;
           }
@@ -302,10 +324,15 @@ __global__ void k_soft_col(SoftArgs A, const float* __restrict__ Ct, const float
 }
 
 // Combine the splits in order.  mean: c_next = S / N (or c if N == 0),
-// N_out = N.  grad: G_out = -2 * sum (the dL/dc of the pass).
+// N_out = N.  grad: G_out = -2 * sum (the dL/dc of the pass), times
+// scale[b] if given; with Nn and Gin (an update step of the backward), a
+// centroid whose weights all underflowed (Nn = 0) kept its position in the
+// forward (c^{t+1} = c^t), so the upstream gradient Gin of c^{t+1} also
+// flows on to c^t unchanged.
 __global__ void k_soft_reduce(SoftArgs A, int D, int mode, const float* __restrict__ Ct,
                               float* __restrict__ Cnext, float* __restrict__ Nout,
-                              float* __restrict__ Gout) {
+                              float* __restrict__ Gout, const float* __restrict__ Nn,
+                              const float* __restrict__ Gin, const double* __restrict__ scale) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)A.B * A.k) return;
   const int b = (int)(idx / A.k), j = (int)(idx % A.k);
@@ -320,7 +347,10 @@ __global__ void k_soft_reduce(SoftArgs A, int D, int mode, const float* __restri
       for (int a = 0; a < D; ++a)
         Cnext[idx * D + a] = t[3] > 0.0 ? (float)(t[a] / t[3]) : Ct[idx * D + a];
   } else {
-    for (int a = 0; a < D; ++a) Gout[idx * D + a] = (float)(-2.0 * t[a]);
+    const double f = scale ? -2.0 * scale[b] : -2.0;
+    const bool through = Nn && Gin && !(Nn[idx] > 0.f);
+    for (int a = 0; a < D; ++a)
+      Gout[idx * D + a] = (float)(f * t[a]) + (through ? Gin[idx * D + a] : 0.f);
   }
 }
 
@@ -386,6 +416,14 @@ dkm_status soft_plan(const int64_t* offsets, int B, int d, int k, SoftPlan* P) {
 // scratch laid out in one stream-ordered allocation
 struct SoftScratch {
   void* base = nullptr;
+  cudaStream_t stream = nullptr;
+  // released (stream-ordered) on every exit path of the call that made it
+  ~SoftScratch() {
+    if (base) cudaFreeAsync(base, stream);
+  }
+  SoftScratch() = default;
+  SoftScratch(const SoftScratch&) = delete;
+  SoftScratch& operator=(const SoftScratch&) = delete;
   SoftArgs A{};
   double* loss_part = nullptr;
   double* loss_dev = nullptr;
@@ -403,8 +441,10 @@ dkm_status soft_alloc(const SoftPlan& P, int B, int d, int k, const float* tau, 
          o_lp = o_part + al(sizeof(double) * 4 * (size_t)B * P.ns * k),
          o_ld = o_lp + al(sizeof(double) * (size_t)B * P.gx), o_N = o_ld + al(sizeof(double) * B),
          o_G0 = o_N + al(4 * (size_t)B * k), o_G1 = o_G0 + al(4 * (size_t)B * k * d),
-         o_lab = o_G1 + al(4 * (size_t)B * k * d), total = o_lab + al(4 * n);
+         o_lab = o_G1 + al(4 * (size_t)B * k * d), o_bad = o_lab + al(4 * n),
+         total = o_bad + al(sizeof(int));
   SOFT_CK(cudaMallocAsync(&S->base, total, st));
+  S->stream = st;
   char* c = (char*)S->base;
   SoftArgs& A = S->A;
   A.off = (const int64_t*)(c + o_off);
@@ -422,33 +462,39 @@ dkm_status soft_alloc(const SoftPlan& P, int B, int d, int k, const float* tau, 
   S->G[0] = (float*)(c + o_G0);
   S->G[1] = (float*)(c + o_G1);
   S->labels = (int32_t*)(c + o_lab);
+  A.bad = (int*)(c + o_bad);
+  SOFT_CK(cudaMemsetAsync(A.bad, 0, sizeof(int), st));
   SOFT_CK(cudaMemcpyAsync((void*)A.off, P.off.data(), sizeof(int64_t) * (B + 1),
                           cudaMemcpyHostToDevice, st));
   SOFT_CK(cudaMemcpyAsync((void*)A.tau, tau, sizeof(float) * B, cudaMemcpyDefault, st));
   return DKM_OK;
 }
 
+// Launchers.  A is the scratch's argument block, possibly with the row
+// statistics of one step pointed at the caller's arrays (step_args).
 template <int D, int MODE>
-void launch_row(const SoftScratch& S, const SoftPlan& P, const float* Ct, const float* Cn,
-                const float* Nn, const float* Gn, const double* dloss, float* gP, int32_t* lab,
-                cudaStream_t st) {
-  const size_t smem = sizeof(float4) * (size_t)S.A.k * (MODE == kRowStep ? 3 : 1);
-  k_soft_row<D, MODE><<<dim3(P.gx, S.A.B), kRowThreads, smem, st>>>(S.A, Ct, Cn, Nn, Gn, dloss, gP,
-                                                                   lab, S.loss_part);
+void launch_row(const SoftArgs& A, const SoftScratch& S, const SoftPlan& P, const float* Ct,
+                const float* Cn, const float* Nn, const float* Gn, const double* dloss, float* gP,
+                int32_t* lab, cudaStream_t st) {
+  const size_t smem = sizeof(float4) * (size_t)A.k * (MODE == kRowStep ? 3 : 1);
+  k_soft_row<D, MODE><<<dim3(P.gx, A.B), kRowThreads, smem, st>>>(A, Ct, Cn, Nn, Gn, dloss, gP,
+                                                                 lab, S.loss_part);
 }
 
 template <int D, int MODE>
-void launch_col(const SoftScratch& S, const SoftPlan& P, const float* Ct, const float* Cn,
+void launch_col(const SoftArgs& A, const SoftPlan& P, const float* Ct, const float* Cn,
                 const float* Nn, const float* Gn, const double* dloss, const int32_t* lab,
                 cudaStream_t st) {
-  const int thr = std::max(32, (S.A.k + 31) / 32 * 32);
-  k_soft_col<D, MODE><<<dim3(P.ns, S.A.B), thr, 0, st>>>(S.A, Ct, Cn, Nn, Gn, dloss, lab);
+  const int thr = std::max(32, (A.k + 31) / 32 * 32);
+  k_soft_col<D, MODE><<<dim3(P.ns, A.B), thr, 0, st>>>(A, Ct, Cn, Nn, Gn, dloss, lab);
 }
 
-void launch_reduce(const SoftScratch& S, int d, int mode, const float* Ct, float* Cnext, float* Nout,
-                   float* Gout, cudaStream_t st) {
-  const int64_t tot = (int64_t)S.A.B * S.A.k;
-  k_soft_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(S.A, d, mode, Ct, Cnext, Nout, Gout);
+void launch_reduce(const SoftArgs& A, int d, int mode, const float* Ct, float* Cnext, float* Nout,
+                   float* Gout, cudaStream_t st, const float* Nn = nullptr,
+                   const float* Gin = nullptr, const double* scale = nullptr) {
+  const int64_t tot = (int64_t)A.B * A.k;
+  k_soft_reduce<<<(int)((tot + 255) / 256), 256, 0, st>>>(A, d, mode, Ct, Cnext, Nout, Gout, Nn,
+                                                          Gin, scale);
 }
 
 dkm_status finish_loss(const SoftScratch& S, const SoftPlan& P, int B, double* loss, cudaStream_t st) {
@@ -460,16 +506,16 @@ dkm_status finish_loss(const SoftScratch& S, const SoftPlan& P, int B, double* l
   return DKM_OK;
 }
 
-// the scratch with the row statistics of step t in the caller's arrays
-// (stats: T x [m | iz] x n_total)
-SoftScratch step_scratch(const SoftScratch& S, const SoftPlan& P, const float* stats, int t) {
-  SoftScratch St = S;
+// the argument block with the row statistics of step t in the caller's
+// arrays (stats: T x [m | iz] x n_total)
+SoftArgs step_args(const SoftScratch& S, const SoftPlan& P, const float* stats, int t) {
+  SoftArgs A = S.A;
   if (stats) {
     const size_t n = (size_t)P.n_total;
-    St.A.m = const_cast<float*>(stats) + (size_t)(2 * t) * n;
-    St.A.iz = const_cast<float*>(stats) + (size_t)(2 * t + 1) * n;
+    A.m = const_cast<float*>(stats) + (size_t)(2 * t) * n;
+    A.iz = const_cast<float*>(stats) + (size_t)(2 * t + 1) * n;
   }
-  return St;
+  return A;
 }
 
 template <int D>
@@ -484,16 +530,16 @@ dkm_status soft_forward_impl(const float* pts, const SoftPlan& P, int B, int k, 
   SOFT_CK(cudaMemcpyAsync(ckpt, init, sizeof(float) * ck, cudaMemcpyDefault, st));
   for (int t = 0; t < T; ++t) {
     const float* Ct = ckpt + t * ck;
-    const SoftScratch St = step_scratch(S, P, stats, t);
-    launch_row<D, kRowStats>(St, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    launch_col<D, kColMean>(St, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-    launch_reduce(St, D, 0, Ct, ckpt + (t + 1) * ck, norms ? norms + (size_t)t * B * k : nullptr,
+    const SoftArgs At = step_args(S, P, stats, t);
+    launch_row<D, kRowStats>(At, S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             st);
+    launch_col<D, kColMean>(At, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    launch_reduce(At, D, 0, Ct, ckpt + (t + 1) * ck, norms ? norms + (size_t)t * B * k : nullptr,
                   nullptr, st);
   }
-  launch_row<D, kRowLoss>(S, P, ckpt + T * ck, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                          st);
+  launch_row<D, kRowLoss>(S.A, S, P, ckpt + T * ck, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, st);
   r = finish_loss(S, P, B, loss, st);
-  cudaFreeAsync(S.base, st);
   if (r != DKM_OK) return r;
   SOFT_CK(cudaGetLastError());
   SOFT_CK(cudaStreamSynchronize(st));
@@ -513,33 +559,33 @@ dkm_status soft_backward_impl(const float* pts, const SoftPlan& P, int B, int k,
   const size_t ck = (size_t)B * k * D;
   // loss stage
   const float* CT = ckpt + T * ck;
-  launch_row<D, kRowLossBwd>(S, P, CT, nullptr, nullptr, nullptr, dl, gp, nullptr, st);
-  launch_col<D, kColLoss>(S, P, CT, nullptr, nullptr, nullptr, dl, nullptr, st);
+  launch_row<D, kRowLossBwd>(S.A, S, P, CT, nullptr, nullptr, nullptr, dl, gp, nullptr, st);
+  launch_col<D, kColLoss>(S.A, P, CT, nullptr, nullptr, nullptr, dl, nullptr, st);
   int cur = 0;
-  launch_reduce(S, D, 1, CT, nullptr, nullptr, S.G[cur], st);
+  launch_reduce(S.A, D, 1, CT, nullptr, nullptr, S.G[cur], st);
   // the updates, last first
   const bool given = stats && norms;   // the forward's per-step statistics
   for (int t = T - 1; t >= 0; --t) {
     const float* Ct = ckpt + t * ck;
     const float* Cn = ckpt + (t + 1) * ck;
-    SoftScratch St = S;
+    SoftArgs At = S.A;
     const float* N = S.N;
     if (given) {
-      St = step_scratch(S, P, stats, t);
-      St.A.use_stats = 1;
+      At = step_args(S, P, stats, t);
+      At.use_stats = 1;
       N = norms + (size_t)t * B * k;
     } else {
-      launch_row<D, kRowStats>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-      launch_col<D, kColMean>(S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-      launch_reduce(S, D, 0, Ct, nullptr, S.N, nullptr, st);
+      launch_row<D, kRowStats>(S.A, S, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                               st);
+      launch_col<D, kColMean>(S.A, P, Ct, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+      launch_reduce(S.A, D, 0, Ct, nullptr, S.N, nullptr, st);
     }
-    launch_row<D, kRowStep>(St, P, Ct, Cn, N, S.G[cur], nullptr, gp, nullptr, st);
-    launch_col<D, kColStep>(St, P, Ct, Cn, N, S.G[cur], nullptr, nullptr, st);
-    launch_reduce(St, D, 1, Ct, nullptr, nullptr, S.G[cur ^ 1], st);
+    launch_row<D, kRowStep>(At, S, P, Ct, Cn, N, S.G[cur], nullptr, gp, nullptr, st);
+    launch_col<D, kColStep>(At, P, Ct, Cn, N, S.G[cur], nullptr, nullptr, st);
+    launch_reduce(At, D, 1, Ct, nullptr, nullptr, S.G[cur ^ 1], st, N, S.G[cur]);
     cur ^= 1;
   }
   SOFT_CK(cudaMemcpyAsync(gi, S.G[cur], sizeof(float) * ck, cudaMemcpyDefault, st));
-  cudaFreeAsync(S.base, st);
   SOFT_CK(cudaGetLastError());
   SOFT_CK(cudaStreamSynchronize(st));
   return DKM_OK;
@@ -554,17 +600,85 @@ dkm_status hard_impl(const float* pts, const SoftPlan& P, int B, int k, const fl
   if (r != DKM_OK) return r;
   S.A.P = pts;
   int32_t* lab = labels ? labels : S.labels;
-  launch_row<D, kRowHard>(S, P, C, nullptr, nullptr, nullptr, nullptr, gp, lab, st);
+  launch_row<D, kRowHard>(S.A, S, P, C, nullptr, nullptr, nullptr, nullptr, gp, lab, st);
   r = finish_loss(S, P, B, loss, st);
-  if (r == DKM_OK && gc) {
-    launch_col<D, kColHard>(S, P, C, nullptr, nullptr, nullptr, nullptr, lab, st);
-    launch_reduce(S, D, 1, C, nullptr, nullptr, gc, st);
-  }
-  cudaFreeAsync(S.base, st);
   if (r != DKM_OK) return r;
+  if (gc) {
+    launch_col<D, kColHard>(S.A, P, C, nullptr, nullptr, nullptr, nullptr, lab, st);
+    launch_reduce(S.A, D, 1, C, nullptr, nullptr, gc, st);
+  }
   SOFT_CK(cudaGetLastError());
   SOFT_CK(cudaStreamSynchronize(st));
   return DKM_OK;
+}
+
+template <int D>
+dkm_status hard_backward_impl(const float* pts, const SoftPlan& P, int B, int k, const float* C,
+                              const int32_t* labels, const double* dloss, float* gp, float* gc,
+                              cudaStream_t st) {
+  SoftScratch S;
+  std::vector<float> ones((size_t)B, 1.f);   // the temperature is unused here
+  dkm_status r = soft_alloc(P, B, D, k, ones.data(), st, &S);
+  if (r != DKM_OK) return r;
+  S.A.P = pts;
+  double* dl = S.loss_dev;   // upstream gradient per cloud, on the device
+  SOFT_CK(cudaMemcpyAsync(dl, dloss, sizeof(double) * B, cudaMemcpyDefault, st));
+  if (gp)
+    launch_row<D, kRowHardBwd>(S.A, S, P, C, nullptr, nullptr, nullptr, dl, gp,
+                               const_cast<int32_t*>(labels), st);
+  if (gc) {
+    launch_col<D, kColHard>(S.A, P, C, nullptr, nullptr, nullptr, nullptr, labels, st);
+    launch_reduce(S.A, D, 1, C, nullptr, nullptr, gc, st, nullptr, nullptr, dl);
+  }
+  int bad = 0;
+  SOFT_CK(cudaGetLastError());
+  SOFT_CK(cudaMemcpyAsync(&bad, S.A.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SOFT_CK(cudaStreamSynchronize(st));
+  if (bad) return soft_fail(DKM_EINVAL, "dkm_hard_sse_backward: a label lies outside [0, k)");
+  return DKM_OK;
+}
+
+// tau_b = frac * squared diagonal of cloud b's bounding box: one CTA per
+// cloud; the extents are FP32 differences of the box corners and the
+// squares are summed in FP64.
+__global__ void __launch_bounds__(512) k_soft_tau(const float* __restrict__ P,
+                                                 const int64_t* __restrict__ off, int d,
+                                                 double frac, float* __restrict__ tau) {
+  __shared__ float s_lo[3][16], s_hi[3][16];
+  const int b = blockIdx.x;
+  const int64_t o0 = off[b], o1 = off[b + 1];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = o0 + threadIdx.x; i < o1; i += blockDim.x)
+    for (int a = 0; a < d; ++a) {
+      const float v = P[i * d + a];
+      lo[a] = fminf(lo[a], v);
+      hi[a] = fmaxf(hi[a], v);
+    }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int a = 0; a < 3; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+    if (lane == 0) {
+      s_lo[a][w] = lo[a];
+      s_hi[a][w] = hi[a];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q = 0.0;
+    for (int a = 0; a < d; ++a) {
+      float l = INFINITY, h = -INFINITY;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+        l = fminf(l, s_lo[a][ww]);
+        h = fmaxf(h, s_hi[a][ww]);
+      }
+      const double e = (double)__fsub_rn(h, l);
+      q += e * e;
+    }
+    tau[b] = (float)(frac * q);
+  }
 }
 
 }  // namespace
@@ -605,6 +719,50 @@ DKM_API dkm_status dkm_soft_backward(const float* points, const int64_t* offsets
                                         grad_points, grad_init, st)
                 : soft_backward_impl<2>(points, P, B, k, ckpt, T, tau, dloss, stats, norms,
                                         grad_points, grad_init, st);
+}
+
+DKM_API dkm_status dkm_hard_sse_backward(const float* points, const int64_t* offsets, int B,
+                                         int d, int k, const float* centroids,
+                                         const int32_t* labels, const double* dloss,
+                                         float* grad_points, float* grad_centroids,
+                                         void* stream) {
+  SoftPlan P;
+  dkm_status r = soft_plan(offsets, B, d, k, &P);
+  if (r != DKM_OK) return r;
+  if (!points || !centroids || !labels || !dloss) return soft_fail(DKM_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  return d == 3 ? hard_backward_impl<3>(points, P, B, k, centroids, labels, dloss, grad_points,
+                                        grad_centroids, st)
+                : hard_backward_impl<2>(points, P, B, k, centroids, labels, dloss, grad_points,
+                                        grad_centroids, st);
+}
+
+DKM_API dkm_status dkm_soft_temperature(const float* points, const int64_t* offsets, int B, int d,
+                                        double frac, float* tau, void* stream) {
+  SoftPlan P;
+  dkm_status r = soft_plan(offsets, B, d, 1, &P);
+  if (r != DKM_OK) return r;
+  if (!points || !tau) return soft_fail(DKM_EINVAL, "null argument");
+  if (!(frac > 0.0) || !std::isfinite(frac)) return soft_fail(DKM_EINVAL, "frac must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* buf = nullptr;
+  const size_t ob = sizeof(int64_t) * (B + 1);
+  SOFT_CK(cudaMallocAsync((void**)&buf, ob + sizeof(float) * B, st));
+  int64_t* doff = (int64_t*)buf;
+  float* dtau = (float*)(buf + ob);
+  cudaError_t e = cudaMemcpyAsync(doff, P.off.data(), ob, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_soft_tau<<<B, 512, 0, st>>>(points, doff, d, frac, dtau);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tau, dtau, sizeof(float) * B, cudaMemcpyDefault, st);
+  cudaFreeAsync(buf, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return soft_fail(DKM_ECUDA, "dkm_soft_temperature", e);
+  }
+  return DKM_OK;
 }
 
 DKM_API dkm_status dkm_hard_sse(const float* points, const int64_t* offsets, int B, int d, int k,

@@ -67,6 +67,12 @@ class dkm_tuning(ctypes.Structure):
                 ("from_cache", ctypes.c_int)]
 
 
+class dkm_peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int), ("sm_clock_mhz", ctypes.c_int),
+                ("fp32_fma_tflops", ctypes.c_double), ("fp32x2_fma_tflops", ctypes.c_double),
+                ("scalar_ms", ctypes.c_float), ("packed_ms", ctypes.c_float)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 # (name, restype, argtypes); "status" functions return dkm_status
@@ -132,6 +138,14 @@ _SIGS = [
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    ("dkm_hard_sse_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+    ("dkm_device_peaks", ctypes.c_int, [ctypes.POINTER(dkm_peaks), ctypes.c_void_p]),
+    ("dkm_soft_temperature", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
 ]
 
 DKM_NOALLOC_MAX_K = 65536
@@ -444,6 +458,39 @@ def dkm_hard_sse(points, offsets, B: int, d: int, k: int, centroids, labels=None
     gc, _k6 = _arr(grad_centroids, "float32", B * k * d, "grad_centroids")
     _check(lib().dkm_hard_sse(p, off, B, d, k, c, lab, ls, gp, gc, ctypes.c_void_p(stream or 0)),
            "dkm_hard_sse")
+
+
+def dkm_hard_sse_backward(points, offsets, B: int, d: int, k: int, centroids, labels, dloss,
+                          grad_points=None, grad_centroids=None, stream: int = 0) -> None:
+    off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
+    n_total = int(offsets[-1])
+    p, _k1 = _arr(points, "float32", n_total * d, "points")
+    c, _k2 = _arr(centroids, "float32", B * k * d, "centroids")
+    lab, _k3 = _arr(labels, "int32", n_total, "labels")
+    dl, _k4 = _arr(dloss, "float64", B, "dloss")
+    gp, _k5 = _arr(grad_points, "float32", n_total * d, "grad_points")
+    gc, _k6 = _arr(grad_centroids, "float32", B * k * d, "grad_centroids")
+    _check(lib().dkm_hard_sse_backward(p, off, B, d, k, c, lab, dl, gp, gc,
+                                       ctypes.c_void_p(stream or 0)), "dkm_hard_sse_backward")
+
+
+def dkm_soft_temperature(points, offsets, B: int, d: int, tau, frac: float = 0.01,
+                         stream: int = 0) -> None:
+    """tau[b] = frac x squared bounding-box diagonal of cloud b (into tau, B floats)."""
+    off, _k0 = _arr(offsets, "int64", B + 1, "offsets")
+    n_total = int(offsets[-1])
+    p, _k1 = _arr(points, "float32", n_total * d, "points")
+    tv, _k2 = _arr(tau, "float32", B, "tau")
+    _check(lib().dkm_soft_temperature(p, off, B, d, float(frac), tv,
+                                      ctypes.c_void_p(stream or 0)), "dkm_soft_temperature")
+
+
+def dkm_device_peaks(stream: int = 0) -> dkm_peaks:
+    """Measured FP32 FMA throughput (scalar and packed f32x2) and SM count."""
+    p = dkm_peaks()
+    _check(lib().dkm_device_peaks(ctypes.byref(p), ctypes.c_void_p(stream or 0)),
+           "dkm_device_peaks")
+    return p
 
 
 def dkm_selftest_wait() -> float:

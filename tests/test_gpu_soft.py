@@ -197,3 +197,70 @@ def test_soft_backward_with_forward_statistics_is_identical(dkm):
         out.append((gp.cpu().numpy(), gi.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert np.all(nm.cpu().numpy() > 0)
+
+
+def test_soft_gradient_passes_through_a_centroid_with_no_weight(dkm):
+    """A centroid whose weights all underflow to zero in step 0 keeps its
+    position (c^1_B = c^0_B), so dL/dc^0_B must equal dL/dc^1_B.  Built so
+    that centroid B has no weight in step 0 but a large one in step 1 (A
+    moves away from the small cluster next to B); the GPU's T = 2 gradient
+    of c^0_B is checked against the FP64 oracle's T = 1 gradient of c^1_B
+    taken from the GPU's own checkpoint c^1."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(91)
+    big = rng.normal(0.0, 0.05, size=(90, 3))
+    small = rng.normal(0.0, 0.05, size=(10, 3)) + np.array([10.0, 0.0, 0.0])
+    P = np.concatenate([big, small]).astype(np.float32)
+    init = np.array([[[10.0, 0.0, 0.0], [19.03, 0.0, 0.0]]], np.float32)   # A, B
+    off = np.array([0, P.shape[0]], np.int64)
+    tau = np.array([0.5], np.float32)
+    B, k, d, T = 1, 2, 3, 2
+    Pt = torch.from_numpy(P).cuda()
+    It = torch.from_numpy(init).cuda()
+    ck = torch.empty((T + 1, B, k, d), dtype=torch.float32, device="cuda")
+    loss = torch.empty(B, dtype=torch.float64, device="cuda")
+    st = torch.empty((T, 2, P.shape[0]), dtype=torch.float32, device="cuda")
+    nm = torch.empty((T, B, k), dtype=torch.float32, device="cuda")
+    dkm.dkm_soft_forward(Pt, off, B, d, k, It, T, tau, ck, loss, stats=st, norms=nm)
+    nm = nm.cpu().numpy()
+    ck = ck.cpu().numpy()
+    assert nm[0, 0, 1] == 0.0 and nm[1, 0, 1] > 0.5   # no weight in step 0, some in step 1
+    assert np.array_equal(ck[1, 0, 1], init[0, 1])     # B kept its position
+    for kw in (dict(), dict(stats=st, norms=torch.from_numpy(nm).cuda())):
+        gp = torch.empty_like(Pt)
+        gi = torch.empty_like(It)
+        dkm.dkm_soft_backward(Pt, off, B, d, k, torch.from_numpy(ck).cuda(), T, tau,
+                              np.ones(1), gp, gi, **kw)
+        _, _, gC1 = sk.soft_backward(P.astype(np.float64), ck[1, 0].astype(np.float64),
+                                     float(tau[0]), 1)
+        g = gi.cpu().numpy()[0, 1]
+        assert np.linalg.norm(gC1[1]) > 1e-2
+        assert _rel(g, gC1[1]) <= GRAD_RTOL
+
+
+def test_hard_sse_backward_scales_and_checks_labels(dkm):
+    """dkm_hard_sse_backward: gradients scale with the upstream gradient of
+    each cloud, and a label outside [0, k) is an error."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(71)
+    clouds = [synth.gaussian_mixture_3d(n, 4, rng) for n in (700, 1300)]
+    pts, P, init, off, tau = _batch(clouds, 6, 72)
+    B, k, d = init.shape
+    Pt = torch.from_numpy(P).cuda()
+    Ct = torch.from_numpy(init).cuda()
+    lab = torch.empty(P.shape[0], dtype=torch.int32, device="cuda")
+    loss = torch.empty(B, dtype=torch.float64, device="cuda")
+    dkm.dkm_hard_sse(Pt, off, B, d, k, Ct, lab, loss)
+    dl = np.array([-0.25, 3.0])
+    gp = torch.empty_like(Pt)
+    gc = torch.empty_like(Ct)
+    dkm.dkm_hard_sse_backward(Pt, off, B, d, k, Ct, lab, dl, gp, gc)
+    for b, Pb in enumerate(pts):
+        _, _, gP, gC = sk.hard_sse_grad(Pb.astype(np.float64), init[b].astype(np.float64))
+        assert _rel(gp.cpu().numpy()[off[b]:off[b + 1]], dl[b] * gP) <= GRAD_RTOL
+        assert _rel(gc.cpu().numpy()[b], dl[b] * gC) <= GRAD_RTOL
+    bad = lab.clone()
+    bad[5] = k
+    with pytest.raises(dkm.DkmError) as e:
+        dkm.dkm_hard_sse_backward(Pt, off, B, d, k, Ct, bad, dl, gp, gc)
+    assert e.value.status == dkm.DKM_EINVAL

@@ -40,8 +40,12 @@ def _noalloc(dkm, pts, C):
 
 def test_noalloc_step_matches_assign_and_update(dkm):
     problems = [synth.lidar3d(seed=51, n=60_011, k=150, n_objects=20),
-                synth.geo2d_blobs(seed=52, n=20_003, k=37)]
-    for w in problems:   # two calls in a row, different n, d and k
+                synth.geo2d_blobs(seed=52, n=20_003, k=37),
+                # centroids staged in three shared-memory rounds, the last partial
+                synth.lidar3d(seed=53, n=30_007, k=2_500, n_objects=30),
+                # the largest k the fixed scratch holds
+                synth.geo2d_blobs(seed=54, n=70_001, k=dkm.DKM_NOALLOC_MAX_K)]
+    for w in problems:   # calls in a row, different n, d and k
         lab_na, C_na, sse_na = _noalloc(dkm, w.points, w.init)
         ctx = make_ctx(dkm, w.points, w.k)
         lab_ref, sse_ref, _ = gpu_assign(dkm, ctx, w.init)
@@ -50,3 +54,28 @@ def test_noalloc_step_matches_assign_and_update(dkm):
         tol = CENTROID_TOL * extent(w.points)
         assert np.abs(C_na.astype(np.float64) - C_ref).max() <= tol
         assert abs(sse_na - sse_ref) <= SSE_RTOL * sse_ref
+
+
+def test_noalloc_step_rejects_non_finite_input(dkm):
+    """A NaN point or an infinite centroid is reported as DKM_EINVAL (the
+    status is read back with the SSE); labels are -1 and the centroids pass
+    through.  The next call with clean input works again."""
+    torch = torch_cuda()
+    w = synth.geo2d_blobs(seed=55, n=5_003, k=20)
+    for which in ("points", "centroids"):
+        P = w.points.copy()
+        C = w.init.copy()
+        if which == "points":
+            P[1234, 1] = np.nan
+        else:
+            C[7, 0] = np.inf
+        n, d = P.shape
+        C_out = torch.zeros(w.k * d, dtype=torch.float32, device="cuda")
+        lab = torch.zeros(n, dtype=torch.int32, device="cuda")
+        with pytest.raises(dkm.DkmError) as ei:
+            dkm.dkm_lloyd_step_noalloc(dev(P), n, d, w.k, dev(C), C_out, lab)
+        assert ei.value.status == dkm.DKM_EINVAL
+        assert np.all(lab.cpu().numpy() == -1)
+        assert np.array_equal(C_out.cpu().numpy().reshape(w.k, d), C)
+    lab_na, C_na, sse_na = _noalloc(dkm, w.points, w.init)
+    assert lab_na.min() >= 0 and np.isfinite(sse_na)
