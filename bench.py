@@ -62,10 +62,79 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+class NvmlClocks:
+    """SM clock, power and clock-event reasons read through NVML (the
+    driver's libnvidia-ml, loaded with ctypes) every `period` seconds on a
+    background thread: enough samples even inside a timed region of a
+    fraction of a second.  Only reads; changes no setting."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu: int, period: float = 0.01):
+        import ctypes
+        import threading
+        self.ct = ctypes
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None or lib.nvmlInit_v2() != 0:
+            raise RuntimeError("NVML not available")
+        self.lib = lib
+        cnt = ctypes.c_uint(0)
+        lib.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+        idx = gpu if cnt.value > gpu else 0
+        self.h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(self.h)) != 0:
+            raise RuntimeError("NVML device handle")
+        self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        mx = ctypes.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        self.period = period
+        self.rows = []
+        self.stop = threading.Event()
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+
+    def _loop(self):
+        ct = self.ct
+        mhz, mw, rs = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        while not self.stop.is_set():
+            self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz))
+            self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+            self.reason_fn(self.h, ct.byref(rs))
+            self.rows.append((time.time(), float(mhz.value), mw.value / 1000.0, int(rs.value)))
+            time.sleep(self.period)
+
+    def start(self):
+        self.thread.start()
+
+    def finish(self):
+        self.stop.set()
+        self.thread.join(timeout=2)
+
+    def summary(self, window):
+        rows = [r for r in self.rows if window[0] <= r[0] <= window[1]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"],
+                    "samples": 0, "source": "nvml"}
+        reasons = sorted({name for r in rows for bit, name in self.REASONS.items() if r[3] & bit})
+        return {"sm_mhz": float(np.median([r[1] for r in rows])), "sm_max_mhz": self.max_mhz,
+                "sm_mhz_min": min(r[1] for r in rows), "power_w_max": max(r[2] for r in rows),
+                "reasons": reasons, "samples": len(rows), "source": "nvml",
+                "period_ms": self.period * 1e3}
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle samples.  Started before the warm-up (the
-    tool's start-up must not overlap the timed region); summary() keeps the
-    samples taken inside the timed window (the nearest ones if none)."""
+    """Clock / throttle samples during the timed region: NVML every 10 ms
+    when the driver library loads, else nvidia-smi every 100 ms.  Started
+    before the warm-up (the tool's start-up must not overlap the timed
+    steps); summary() keeps the samples taken inside the timed window (the
+    nearest one if none)."""
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -74,20 +143,29 @@ class ClockSampler:
         self.gpu = gpu
         self.proc = None
         self.path = None
+        self.nvml = None
 
     def __enter__(self):
+        try:
+            self.nvml = NvmlClocks(self.gpu)
+            self.nvml.start()
+            return self
+        except Exception:
+            self.nvml = None
         fd, self.path = tempfile.mkstemp(prefix="dkm_clocks_", suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.nvml.finish()
         if self.proc is not None:
             self.proc.send_signal(signal.SIGTERM)
             try:
@@ -96,6 +174,8 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self, window=None):
+        if self.nvml is not None:
+            return self.nvml.summary(window)
         rows = []
         try:
             with open(self.path) as f:
@@ -129,7 +209,28 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "source": "nvidia-smi"}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu, else platform)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def dist_env():
@@ -152,13 +253,25 @@ def load_workload():
                          max_iter=WORKLOAD["iterations"])
 
 
-def cpu_sample_run(w, m: int, seed: int = 0):
+def _oracle(single_thread: bool):
+    """The oracle as it stands: the OpenMP build, or the same source built
+    without OpenMP (one host thread)."""
+    import oracle
+    if not single_thread:
+        return oracle.get()
+    path = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "_build",
+                        "libdkm_oracle_st.so")
+    if not os.path.exists(path):
+        oracle.build(out=path, openmp=False)
+    return oracle.Oracle(path)
+
+
+def cpu_sample_run(w, m: int, seed: int = 0, single_thread: bool = False):
     """The oracle as it stands on a bounded sample: one Lloyd iteration
     (brute-force FP64 assignment against all k centroids + update) of m
     points drawn from the workload.  Returns (point-iterations/s, seconds,
     threads)."""
-    import oracle
-    o = oracle.get()
+    o = _oracle(single_thread)
     if m >= w.n:
         m = w.n
         sample = w.points
@@ -169,7 +282,7 @@ def cpu_sample_run(w, m: int, seed: int = 0):
     t0 = time.perf_counter()
     o.fit(sample, w.init.astype(np.float64), 1, early_stop=False)
     dt = time.perf_counter() - t0
-    return m / dt, dt, o.num_threads()
+    return m / dt, dt, (1 if single_thread else o.num_threads())
 
 
 def run_reference(args):
@@ -286,21 +399,9 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
 
     for _ in range(2):
         step()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    a_ms, s_ms, u_ms, setup_ms = [], [], [], []
     torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    T = dkm.dkm_last_timings(ctx)   # the last timed step's profiled (middle) pass
-    a_ms.append(T.assign_ms)
-    s_ms.append(T.search_ms)
-    u_ms.append(T.update_ms)
-    setup_ms.append(T.setup_ms)
-    t_step = ev0.elapsed_time(ev1) / 1e3 / steps
+    t_step, per = timed_steps(step, stream, steps, ctx, dkm)
+    s_ms, a_ms, u_ms, setup_ms = (per[:, i] for i in range(4))
     st = dkm.dkm_last_stats(ctx)
     per_pass = float(np.mean(s_ms) + np.mean(a_ms) + np.mean(u_ms))
     ob = dkm.dkm_default_options(early_stop=0, profile=1, algo=dkm.DKM_ALGO_BRUTE,
@@ -339,7 +440,7 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
             "launches_per_pass": 3}
 
 
-def bench_soft(dkm, torch, dev, stream, steps: int):
+def bench_soft(dkm, torch, dev, stream, steps: int, peaks_dev=None):
     """The differentiable workload: 64 clouds x 16384 points, k = 256; soft
     k-means with T = 10 unrolled steps forward + backward, and the hard SSE
     with its gradient."""
@@ -386,7 +487,148 @@ def bench_soft(dkm, torch, dev, stream, steps: int):
     # forward: T + 1 weight passes over n x k distances; backward: recompute
     # + adjoint, about 3 passes per step
     out["soft_point_centroid_pairs_per_s"] = n * k * (T + 1) / (out["soft_forward_backward_ms"] * 1e-3)
+    if peaks_dev is not None:
+        fl = soft_flops_per_pair(T) * n * k
+        ach = fl / (out["soft_forward_backward_ms"] * 1e-3) / 1e12
+        out["alu_roofline"] = {"bound": "alu", "kernel": "soft forward + backward (all passes)",
+                               "achieved": ach, "peak": peaks_dev.fp32_fma_tflops,
+                               "unit": "TFLOP/s", "frac": ach / peaks_dev.fp32_fma_tflops,
+                               "flops_per_pair": soft_flops_per_pair(T),
+                               "peak_source": "measured scalar FP32 FMA rate "
+                                              "(dkm_device_peaks); the soft kernels are scalar"}
+        hf = BRUTE_FLOPS_PER_PAIR * n * k / (out["hard_sse_with_grad_ms"] * 1e-3) / 1e12
+        out["hard_alu_roofline"] = {"bound": "alu", "achieved": hf,
+                                    "peak": peaks_dev.fp32_fma_tflops, "unit": "TFLOP/s",
+                                    "frac": hf / peaks_dev.fp32_fma_tflops,
+                                    "flops_per_pair": BRUTE_FLOPS_PER_PAIR}
     return out
+
+
+# FP32 floating-point operations per (point, centroid) pair, counted in the
+# kernel source (an FMA counts 2, a min/compare 0, the exponential 1 for its
+# argument scaling): distance 8; soft forward step 39 (row statistics 20,
+# column mean 19), forward loss 34, backward loss stage 70 (row 47, column
+# 23), backward step 82 with the forward's statistics (row 47, column 35).
+BRUTE_FLOPS_PER_PAIR = 8
+
+
+def soft_flops_per_pair(T: int) -> int:
+    return 39 * T + 34 + 70 + 82 * T
+
+
+def timed_steps(step, stream, steps, ctx, dkm):
+    """Run `steps` steps between two CUDA events on the stream; after each
+    step, read that step's profiled-pass kernel times (dkm_run returns after
+    its outputs are ready, so this costs host microseconds)."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    per = []
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+        T = dkm.dkm_last_timings(ctx)
+        per.append((T.search_ms, T.assign_ms, T.update_ms, T.setup_ms))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3 / steps, np.array(per, np.float64)
+
+
+def bench_2d(dkm, torch, dev, stream, name: str, steps: int, hbm: float):
+    """A 2D side line (geo2d-blobs: early stop; geo2d-roads: 50 fixed
+    passes): point-iterations/s with the index the autotuner picks, the
+    per-pass HBM fraction and the brute-force ratio on the same GPU."""
+    from paper_2412_02244_gb300 import synth
+    w = synth.by_name(name)
+    n, d, k = w.n, w.d, w.k
+    early = 1 if name == "geo2d-blobs" else 0
+    iters = 20 if early else 50
+    # bytes per point of one assignment: the point, the label written, and
+    # the previous label read when the early stop needs the change count
+    bpp = 4 * d + 4 + (4 if early else 0)
+    pts = torch.from_numpy(w.points).to(dev)
+    init = torch.from_numpy(w.init).to(dev)
+    C = torch.empty(k * d, dtype=torch.float32, device=dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    opts = dkm.dkm_default_options(early_stop=early, profile=1, stream=stream.cuda_stream)
+    ctx = dkm.dkm_create(pts, n, d, k, opts)
+    tune = dkm.dkm_autotune(ctx, init, passes=3, use_cache=False)
+    passes = [0]
+
+    def step():
+        dkm.dkm_setup(ctx, pts)
+        it, _ = dkm.dkm_run(ctx, init, iters, C, lab)
+        passes[0] = it
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    t_step, per = timed_steps(step, stream, steps, ctx, dkm)
+    it = passes[0]
+    s_ms, a_ms, u_ms = (float(per[:, i].mean()) for i in range(3))
+    per_pass = s_ms + a_ms + u_ms
+    ob = dkm.dkm_default_options(early_stop=0, profile=1, algo=dkm.DKM_ALGO_BRUTE,
+                                 stream=stream.cuda_stream)
+    cb = dkm.dkm_create(pts, n, d, k, ob)
+    Cb = torch.empty(k * d, dtype=torch.float32, device=dev)
+    lb = torch.empty(n, dtype=torch.int32, device=dev)
+    dkm.dkm_run(cb, C, 2, Cb, lb)
+    dkm.dkm_run(cb, C, 2, Cb, lb)
+    Tb = dkm.dkm_last_timings(cb)
+    per_b = Tb.search_ms + Tb.assign_ms + Tb.update_ms
+    cb.close()
+    ctx.close()
+    return {"config": {"workload": name, "n": n, "d": d, "k": k,
+                       "iterations": ("<= 20, early stop" if early else iters), "seed": w.seed},
+            "value": n * it / t_step, "unit": METRIC, "ms_per_step": t_step * 1e3,
+            "passes_per_step": it, "per_pass_ms": per_pass, "search_ms": s_ms, "assign_ms": a_ms,
+            "update_ms": u_ms, "setup_ms": float(per[:, 3].mean()),
+            "hbm_frac_per_pass": n * bpp / (per_pass * 1e-3) / 1e9 / hbm,
+            "k_assign_hbm_frac": n * bpp / (a_ms * 1e-3) / 1e9 / hbm,
+            "algorithmic_bytes_per_point": bpp,
+            "brute_force": {"ms_per_pass": per_b,
+                            "speedup_indexed_over_brute": per_b / per_pass if per_pass else None},
+            "tuning": {"cells_per_centroid": tune.cells_per_centroid,
+                       "tile_cut_div": tune.tile_cut_div, "row_filter_min": tune.row_filter_min,
+                       "sort_max": tune.sort_max, "tile_group": tune.tile_group,
+                       "stay_test": tune.stay_test}}
+
+
+def bench_cold(dkm, torch, dev, stream, w, tune, iters):
+    """The first step a one-shot user sees: a fresh context (candidate lists
+    empty, so pass 1 searches from scratch), one dkm_setup + dkm_run timed
+    with CUDA events; and dkm_fit end to end (create + run + destroy, device
+    buffers) timed on the host."""
+    n, d, k = w.n, w.d, w.k
+    pts = torch.from_numpy(w.points).to(dev)
+    init = torch.from_numpy(w.init).to(dev)
+    C = torch.empty(k * d, dtype=torch.float32, device=dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    opts = dkm.dkm_default_options(early_stop=0, profile=0, stream=stream.cuda_stream)
+    ctx = dkm.dkm_create(pts, n, d, k, opts)
+    if tune is not None:
+        dkm.dkm_set_tuning(ctx, tune)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dkm.dkm_setup(ctx, pts)
+    dkm.dkm_run(ctx, init, iters, C, lab)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cold_ms = e0.elapsed_time(e1)
+    ctx.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dkm.dkm_fit(pts, n, d, k, init, iters, C, lab,
+                dkm.dkm_default_options(early_stop=0, stream=stream.cuda_stream))
+    torch.cuda.synchronize()
+    fit_ms = (time.perf_counter() - t0) * 1e3
+    return {"step_ms": cold_ms, "value": n * iters / (cold_ms * 1e-3), "unit": METRIC,
+            "dkm_fit_ms": fit_ms,
+            "what": "one dkm_setup + dkm_run on a fresh context (no candidate lists kept from "
+                    "an earlier step; the autotuned setting applied); dkm_fit = create + run + "
+                    "destroy with default settings, host wall time"}
 
 
 def run_ours(args):
@@ -433,9 +675,6 @@ def run_ours(args):
         dkm.dkm_setup(ctx, pts)
         return dkm.dkm_run(ctx, init, iters, C, lab)
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    assign_ms, search_ms, update_ms, setup_ms = [], [], [], []
     # the clock sampler starts before the warm-up: its start-up (NVML
     # initialisation) would otherwise overlap the timed steps
     with ClockSampler(local) as clk:
@@ -447,22 +686,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         w0 = time.time()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            it, sse = step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        t_step, per = timed_steps(step, stream, args.steps, ctx, dkm)
         w1 = time.time()
-        time.sleep(0.25)   # let a sample land after the window (for short timed regions)
-    if args.profile:
-        # per-kernel times of the last timed step (CUDA events around the
-        # kernels of its middle pass, recorded inside the captured graph)
-        T = dkm.dkm_last_timings(ctx)
-        assign_ms.append(T.assign_ms)
-        search_ms.append(T.search_ms)
-        update_ms.append(T.update_ms)
-        setup_ms.append(T.setup_ms)
-    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+        time.sleep(0.25)
     times = [t_step]
     if dist:
         tt = torch.tensor([t_step], device=dev)
@@ -479,7 +705,7 @@ def run_ours(args):
     dkm.dkm_setup(ctx, pts_h)
     dkm.dkm_run(ctx, init_h, iters, C_h, lab_h)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(3, min(args.steps, 10))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         dkm.dkm_setup(ctx, pts_h)
@@ -492,6 +718,12 @@ def run_ours(args):
         t_e2e = float(tt.item())
     e2e_value = ws * n * iters / t_e2e
 
+    peaks_dev = None
+    try:
+        peaks_dev = dkm.dkm_device_peaks(stream.cuda_stream)
+    except Exception:
+        peaks_dev = None
+
     # brute-force Lloyd on the same GPU, from the same converged centroids
     brute = None
     if rank == 0 and not args.no_brute:
@@ -500,6 +732,7 @@ def run_ours(args):
         cb = dkm.dkm_create(pts, n, d, k, ob)
         Cb = torch.empty(k * d, dtype=torch.float32, device=dev)
         lb = torch.empty(n, dtype=torch.int32, device=dev)
+        dkm.dkm_run(cb, C, 2, Cb, lb)
         dkm.dkm_run(cb, C, 2, Cb, lb)
         Tb = dkm.dkm_last_timings(cb)
         oi = dkm.dkm_default_options(early_stop=0, profile=1, stream=stream.cuda_stream)
@@ -514,6 +747,15 @@ def run_ours(args):
         brute = {"ms_per_iteration": per_b, "indexed_ms_per_iteration": per_i,
                  "speedup_indexed_over_brute": per_b / per_i if per_i > 0 else None,
                  "from": "converged centroids of the timed run, 2 passes each"}
+        if peaks_dev is not None and Tb.assign_ms > 0:
+            ach = BRUTE_FLOPS_PER_PAIR * n * k / (Tb.assign_ms * 1e-3) / 1e12
+            brute["alu_roofline"] = {
+                "bound": "alu", "kernel": "k_assign (brute force)", "achieved": ach,
+                "peak": peaks_dev.fp32x2_fma_tflops, "unit": "TFLOP/s",
+                "frac": ach / peaks_dev.fp32x2_fma_tflops,
+                "peak_source": "measured packed f32x2 FMA rate (dkm_device_peaks); the kernel's "
+                               "distances use packed f32x2 arithmetic",
+                "flops_per_pair": BRUTE_FLOPS_PER_PAIR}
         cb.close()
         ci.close()
 
@@ -533,8 +775,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_job * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": WORKLOAD}
-    if args.profile and assign_ms:
-        a_ms = float(np.mean(assign_ms))
+    if args.profile and len(per):
+        s_ms, a_ms, u_ms = (float(per[:, i].mean()) for i in range(3))
         achieved = n * ASSIGN_BYTES_PER_POINT / (a_ms * 1e-3) / 1e9
         traffic = None
         if NCU_TRAFFIC and NCU_TRAFFIC.get("sha") == kernel_sha():
@@ -543,14 +785,18 @@ def run_ours(args):
                             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                             "peak_source": src, "traffic": traffic,
                             "algorithmic_bytes_per_launch": n * ASSIGN_BYTES_PER_POINT,
-                            "launch_ms": a_ms}
-        per_iter = float(np.mean(search_ms) + np.mean(assign_ms) + np.mean(update_ms))
-        line["per_iteration"] = {"ms": per_iter, "search_ms": float(np.mean(search_ms)),
-                                 "assign_ms": a_ms, "update_ms": float(np.mean(update_ms)),
+                            "launch_ms": a_ms, "launch_ms_min": float(per[:, 1].min()),
+                            "launch_ms_max": float(per[:, 1].max()),
+                            "launches_averaged": int(len(per)),
+                            "how": "CUDA events around k_assign of the middle pass of every "
+                                   "timed step, inside the run graph, averaged"}
+        per_iter = s_ms + a_ms + u_ms
+        line["per_iteration"] = {"ms": per_iter, "search_ms": s_ms, "assign_ms": a_ms,
+                                 "update_ms": u_ms,
                                  "point_iterations_per_s": n / (per_iter * 1e-3),
                                  "hbm_frac_of_iteration": n * ASSIGN_BYTES_PER_POINT
                                  / (per_iter * 1e-3) / 1e9 / hbm,
-                                 "setup_ms": float(np.mean(setup_ms))}
+                                 "setup_ms": float(per[:, 3].mean())}
     if tune is not None:
         line["tuning"] = {"cells_per_centroid": tune.cells_per_centroid,
                           "tile_cut_div": tune.tile_cut_div,
@@ -567,26 +813,49 @@ def run_ours(args):
                        "stayed_tiles": stats.stayed_tiles,
                        "tiles": stats.tiles, "tile_level": stats.tile_level,
                        "grid_overflow": stats.grid_overflow}
+    line["steady_state"] = ("every timed step repeats dkm_setup + dkm_run on the same context: "
+                            "the candidate lists of the previous step seed pass 1's search "
+                            "bound (see 'cold' for a fresh context)")
     if brute:
         line["brute_force"] = brute
     line["e2e"] = {"value": e2e_value, "unit": METRIC,
                    "h2d_bytes_per_step": n * d * 4 + k * d * 4,
                    "d2h_bytes_per_step": n * 4 + k * d * 4, "steps": e2e_steps}
     line["gpu_launches"] = launches_per_step(iters) * args.steps
-    line["clocks"] = clk.summary(window=(w0, w1))
+    clocks = clk.summary(window=(w0, w1))
+    if clocks.get("sm_mhz"):
+        clocks["kcycles_per_step"] = t_job * 1e3 * clocks["sm_mhz"]
+    line["clocks"] = clocks
+    if peaks_dev is not None:
+        line["device"] = {"sm_count": peaks_dev.sm_count, "sm_clock_mhz": peaks_dev.sm_clock_mhz,
+                          "fp32_fma_tflops": peaks_dev.fp32_fma_tflops,
+                          "fp32x2_fma_tflops": peaks_dev.fp32x2_fma_tflops,
+                          "how": "dkm_device_peaks: FMA-chain kernels, CUDA events"}
     if ws == 1 and not args.no_cpu_baseline:
         v, dt, thr = cpu_sample_run(w, args.cpu_sample)
+        m1 = max(1, args.cpu_sample // 16)
+        v1, dt1, _ = cpu_sample_run(w, m1, seed=1, single_thread=True)
         line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle",
+                                "cpu_model": cpu_model(),
                                 "sample": f"one FP64 brute-force Lloyd iteration (assignment "
                                           f"against all k=10000 centroids + update) of "
                                           f"{min(args.cpu_sample, n)} of the workload's {n} "
-                                          f"points ({dt:.1f} s)"}
+                                          f"points ({dt:.1f} s)",
+                                "single_thread": {"value": v1, "unit": METRIC, "cores": 1,
+                                                  "sample": f"the same iteration on {m1} "
+                                                            f"points, the oracle built without "
+                                                            f"OpenMP ({dt1:.1f} s)"}}
     if ablations:
         line["ablations"] = ablations
     if ws == 1 and not args.no_extra:
+        line["cold"] = bench_cold(dkm, torch, dev, stream, w, tune, iters)
         ctx.close()
+        side = max(3, min(args.steps, 10))
+        line["geo2d_blobs"] = bench_2d(dkm, torch, dev, stream, "geo2d-blobs", side, hbm)
+        line["geo2d_roads"] = bench_2d(dkm, torch, dev, stream, "geo2d-roads", side, hbm)
         line["batched"] = bench_batched(dkm, torch, dev, stream, max(2, min(args.steps, 5)), hbm)
-        line["differentiable"] = bench_soft(dkm, torch, dev, stream, max(2, min(args.steps, 5)))
+        line["differentiable"] = bench_soft(dkm, torch, dev, stream, max(2, min(args.steps, 5)),
+                                            peaks_dev)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -598,13 +867,13 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", type=int, default=1,
                     help="record per-kernel CUDA events around the middle pass of every "
                          "timed step, inside the run graph (roofline)")
-    ap.add_argument("--cpu-sample", type=int, default=10_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=4_000_000)
     ap.add_argument("--ref-sample", type=int, default=500_000)
     ap.add_argument("--no-brute", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

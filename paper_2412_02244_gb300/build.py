@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdkm.so")
-SOURCES = ["dkm_setup.cu", "dkm_iter.cu", "dkm_api.cu", "dkm_noalloc.cu", "dkm_soft.cu"]
+SOURCES = ["dkm_setup.cu", "dkm_iter.cu", "dkm_api.cu", "dkm_noalloc.cu", "dkm_soft.cu",
+           "dkm_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
           "--expt-relaxed-constexpr"]
