@@ -120,6 +120,7 @@ typedef struct {
     int64_t tiles;              /* tiles of the point index (<= 256 points each) */
     int tile_level;             /* Morton level whose cubes bound the tiles */
     int passes;                 /* assignment passes of the last dkm_run */
+    int64_t stayed_points;      /* points that passed the point stay test, last pass */
 } dkm_stats;
 
 typedef struct dkm_ctx dkm_ctx;
@@ -282,9 +283,13 @@ typedef struct {
     /* the bound layer (Section IV-A): 1 = before searching, a tile whose
      * points all had label a in the last pass keeps a for every point when
      * its box lies within half the distance from c_a to the nearest other
-     * centroid (maxd(box, c_a) < cb[a] / 2, cb from a grid kNN(2) over
-     * the centroids after each update); such a tile skips the grid search.
-     * Only with tile_group = 1; default 0 */
+     * centroid (maxd(box, c_a) < cb[a] / 2, Eq. interbound; cb from a grid
+     * kNN(2) over the centroids after each update, started inside a run
+     * from the bound ub = cb[j] + Delta[j] + max(Delta) of Eq. ub); such a
+     * tile skips the grid search.  2 = also the point test of Eq.
+     * interbound1 in the assignment: a point within cb[a] / 2 of its last
+     * centroid keeps it, and a row of 64 points that all keep theirs skips
+     * the candidate evaluation.  Only with tile_group = 1; default 0 */
     int stay_test;
     /* dkm_autotune only: mean ms per Lloyd pass of the chosen setting and
      * of the setting the context had before, configurations timed, and
@@ -306,7 +311,7 @@ DKM_API dkm_status dkm_set_tuning(dkm_ctx* ctx, const dkm_tuning* tuning);
  * Measure and apply the fastest setting for this context: coordinate
  * descent over cells_per_centroid {0.5, 1, 2, 4}, tile_cut_div
  * {1, 2, 4, 8, 16, 32}, row_filter_min {16, 32, 48, 96, 256}, sort_max
- * {0, 16, 32}, tile_group {1, 2, 4, 8, 16} and stay_test {0, 1}, each
+ * {0, 16, 32}, tile_group {1, 2, 4, 8, 16} and stay_test {0, 1, 2}, each
  * setting timed (CUDA events, best of two) over `passes` Lloyd passes
  * (1 .. 64, no early stop) from init_centroids.  The context's labels and
  * centroids are overwritten by those runs.  With use_cache = 1 a setting

@@ -168,7 +168,7 @@ struct Layout {
 // Offsets of every buffer in the arena, shared by plan and create.
 struct ArenaPlan {
   size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_scratch, tbox, tiles,
-      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, tlab, tl_scratch, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
+      tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, drift, tlab, tl_scratch, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
       st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
       kstage, total;
 };
@@ -205,6 +205,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.ufirst = L.take<int>(tm + 1);
   P.tunit = L.take<int>(tm);
   P.cb2 = L.take<float>(k);
+  P.drift = L.take<float>(k);
   P.tlab = L.take<int>(tm);
   P.tl_scratch = L.take<unsigned>(tiles_scratch_words((int)nw));
   P.level_hist = L.take<unsigned long long>(B * (kMaxLevels + 1));
@@ -290,9 +291,11 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   A.want_stats = 1;
   A.row_filter_min = c->row_filter_min;
   A.sort_max = c->sort_max;
-  A.stay = (c->stay && c->unit_g == 1 && c->opts.algo != DKM_ALGO_BRUTE) ? 1 : 0;
+  A.stay = (c->unit_g == 1 && c->opts.algo != DKM_ALGO_BRUTE) ? c->stay : 0;
   A.cb2 = c->cb2;
   A.tlab = c->tlab;
+  A.drift = c->drift;
+  A.slot_keys = c->k < (1 << 24) ? 1 : 0;
   return A;
 }
 
@@ -432,7 +435,7 @@ dkm_status one_pass(dkm_ctx* c, bool track_changes) {
   DKM_TRY(zero_run_buffers(c, false));
   IterArgs A = iter_args(c, track_changes ? 1 : 0, 0);
   DKM_CK(launch_centroids(A, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream));
-  if (A.stay) DKM_CK(launch_cbound(A, 0, c->d, c->stream));
+  if (A.stay) DKM_CK(launch_cbound(A, 0, c->d, 0, c->stream));
   if (!brute) DKM_CK(launch_search(A, 0, c->d, c->stream));
   DKM_CK(launch_assign(A, c->d, brute, c->stream));
   DKM_CK(launch_collect(A, -1, c->stream));
@@ -513,7 +516,7 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
   do {
     if ((st = zero_run_buffers(c, early != 0)) != DKM_OK) break;
     if ((e = launch_centroids(A0, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream))) break;
-    if (A0.stay && (e = launch_cbound(A0, 0, c->d, c->stream))) break;
+    if (A0.stay && (e = launch_cbound(A0, 0, c->d, 0, c->stream))) break;
     for (int t = 0; t < iters; ++t) {
       const int par = t & 1;
       // a run returns the SSE of its final labels (computed after the
@@ -530,7 +533,7 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
       if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, cudaEventRecordExternal))) break;
       const int insert = !brute && t + 1 < iters;
       if ((e = launch_centroids(A, 1, t, c->d, nullptr, insert, par ^ 1, nullptr, c->stream))) break;
-      if (A.stay && insert && (e = launch_cbound(A, par ^ 1, c->d, c->stream))) break;
+      if (A.stay && insert && (e = launch_cbound(A, par ^ 1, c->d, 1, c->stream))) break;
       if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, cudaEventRecordExternal))) break;
     }
   } while (0);
@@ -861,6 +864,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->ufirst = (int*)(base + P.ufirst);
   c->tunit = (int*)(base + P.tunit);
   c->cb2 = (float*)(base + P.cb2);
+  c->drift = (float*)(base + P.drift);
   c->tlab = (int*)(base + P.tlab);
   c->tl_scratch = (unsigned*)(base + P.tl_scratch);
   c->level_hist = (unsigned long long*)(base + P.level_hist);
@@ -1016,8 +1020,8 @@ dkm_status tuning_check(const dkm_ctx* c, const dkm_tuning& t) {
     return fail(DKM_EINVAL, "sort_max must be in [0, 32] (got %d)", t.sort_max);
   if (t.tile_group < 1 || t.tile_group > 32)
     return fail(DKM_EINVAL, "tile_group must be in [1, 32] (got %d)", t.tile_group);
-  if (t.stay_test != 0 && t.stay_test != 1)
-    return fail(DKM_EINVAL, "stay_test must be 0 or 1 (got %d)", t.stay_test);
+  if (t.stay_test < 0 || t.stay_test > 2)
+    return fail(DKM_EINVAL, "stay_test must be 0, 1 or 2 (got %d)", t.stay_test);
   return DKM_OK;
 }
 
@@ -1194,9 +1198,12 @@ dkm_status autotune_impl(dkm_ctx* c, const float* init, int passes, int use_cach
     DKM_TRY(trial(t));
   }
   if (best.tile_group == 1) {
-    dkm_tuning t = best;
-    t.stay_test = 1 - best.stay_test;
-    DKM_TRY(trial(t));
+    for (int v : {0, 1, 2}) {
+      if (v == best.stay_test) continue;
+      dkm_tuning t = best;
+      t.stay_test = v;
+      DKM_TRY(trial(t));
+    }
   }
   DKM_TRY(apply_tuning(c, best));
   destroy_graph(c);   // the next dkm_run captures with the caller's flags
@@ -1520,6 +1527,7 @@ dkm_status dkm_last_stats(dkm_ctx* c, dkm_stats* out) {
   out->tile_level = c->tile_level;
   out->fallback_tiles = (int64_t)h.last_fallback;
   out->stayed_tiles = (int64_t)h.last_stays;
+  out->stayed_points = (int64_t)h.last_pstays;
   out->grid_overflow = (int64_t)h.grid_ovf;
   out->passes = h.passes;
   return DKM_OK;

@@ -41,7 +41,8 @@ struct Slot {
   unsigned long long cands;     // sum of tile candidate-list lengths
   unsigned long long fallback;  // tiles whose candidate list overflowed
   unsigned long long stays;     // tiles that passed the stay test (no search)
-  unsigned long long pad[4];
+  unsigned long long pstays;    // points that passed the point stay test
+  unsigned long long pad[3];
 };
 
 // Device-resident run state (whole context).
@@ -57,6 +58,7 @@ struct DevState {
   int tiles;             // dkm_setup: tiles of the new point index
   int pad0;
   unsigned long long last_evals, last_cands, last_fallback, last_changed, last_tiles, last_stays;
+  unsigned long long last_pstays;
   unsigned long long grid_ovf;   // centroids put in an overflow list, last rebuild
   double last_sse;               // total SSE of the last pass (against its input centroids)
   double final_sse;              // total SSE of the final labels against the final centroids
@@ -102,6 +104,9 @@ struct CloudRun {
   int s_glob, s_sse;     // fixed-point exponents of the run (fixed_exponents)
   int done;              // early stop reached
   int passes;            // assignment passes executed in the current run
+  // max centroid drift of the cloud in the update of pass t, in slot t & 1
+  // (ordered bits of a non-negative float; the other slot is cleared then)
+  unsigned dmax[2];
   unsigned long long last_changed;
   double last_sse;
   double final_sse;
@@ -160,10 +165,16 @@ struct IterArgs {
   int sort_max;              // lists up to this length (<= 32) are sorted, early exit
   // Stay test (the bound layer): cb2[j] = squared distance from centroid j
   // to the nearest other centroid of its cloud; tlab[t] = the single label
-  // of tile t in its last pass (-1: mixed or unknown).
+  // of tile t in its last pass (-1: mixed or unknown).  stay = 1: the tile
+  // test before the search; 2: also the point test in the assignment.
   int stay;
   float* cb2;
   int* tlab;
+  float* drift;              // per centroid: distance moved by the last update
+  // Total centroids below 2^24: k_assign keys its staged candidates as
+  // (id << 8 | list position) and reads the winners' centroids from shared
+  // memory for the update sums.
+  int slot_keys;
 };
 
 // A tile whose box lies within cb[a]/2 of centroid a (maxd^2 <= kStay *

@@ -50,7 +50,7 @@ cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,
 cudaError_t launch_finalize(const IterArgs& A, int d, const uint32_t* perm, int32_t* labels_out,
                             int do_sse, cudaStream_t s);
 cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream_t s);
-cudaError_t launch_cbound(const IterArgs& A, int par, int d, cudaStream_t s);
+cudaError_t launch_cbound(const IterArgs& A, int par, int d, int use_ub, cudaStream_t s);
 cudaError_t launch_unit_boxes(const float4* tbox, const int* tcloud, const int* ufirst,
                               int n_units, float4* ubox, int* ucloud, int* tunit,
                               cudaStream_t s);
@@ -114,6 +114,7 @@ struct dkm_ctx {
   int* tfirst = nullptr;       // per cloud: its first tile
   int* kcloud = nullptr;
   float* cb2 = nullptr;        // per centroid: squared gap to its nearest other centroid
+  float* drift = nullptr;      // per centroid: distance moved by the last update
   int* tlab = nullptr;         // per tile: single label of its last pass, or -1
   float4* ubox = nullptr;      // per unit box (unit_g > 1)
   int *ucloud = nullptr, *ufirst = nullptr, *tunit = nullptr;

@@ -46,10 +46,11 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long
 // Sums over clouds run in a fixed order, so the totals are deterministic.
 __device__ void collect_pass(const IterArgs& A, int t) {
   __shared__ double s_sse[kBlockThreads / 32];
-  __shared__ unsigned long long s_part[6][kBlockThreads / 32];
+  __shared__ unsigned long long s_part[7][kBlockThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double sse = 0.0;
-  unsigned long long v[6] = {0, 0, 0, 0, 0, 0};   // changed, evals, cands, fallback, clouds run, stays
+  // changed, evals, cands, fallback, clouds run, stayed tiles, stayed points
+  unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < A.B; b += blockDim.x) {
     CloudRun& r = A.crun[b];
     if (t >= 0 && r.passes != t + 1) continue;   // the cloud stopped earlier
@@ -80,24 +81,24 @@ __device__ void collect_pass(const IterArgs& A, int t) {
   if (t != -2) {
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
       Slot& s = A.slots[i];
-      v[1] += s.evals; v[2] += s.cands; v[3] += s.fallback; v[5] += s.stays;
-      s.evals = 0; s.cands = 0; s.fallback = 0; s.stays = 0;
+      v[1] += s.evals; v[2] += s.cands; v[3] += s.fallback; v[5] += s.stays; v[6] += s.pstays;
+      s.evals = 0; s.cands = 0; s.fallback = 0; s.stays = 0; s.pstays = 0;
     }
   }
   for (int o = 16; o > 0; o >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, o);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < 7; ++q) {
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     if (lane == 0) s_part[q][w] = v[q];
   }
   if (lane == 0) s_sse[w] = sse;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long tot[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long tot[7] = {0, 0, 0, 0, 0, 0, 0};
     double tsse = 0.0;
     for (int ww = 0; ww < (int)(blockDim.x / 32); ++ww) {
       tsse += s_sse[ww];
-      for (int q = 0; q < 6; ++q) tot[q] += s_part[q][ww];
+      for (int q = 0; q < 7; ++q) tot[q] += s_part[q][ww];
     }
     if (t == -2) {   // final SSE of a run: leave the last-pass counters alone
       A.st->final_sse = tsse;
@@ -108,6 +109,7 @@ __device__ void collect_pass(const IterArgs& A, int t) {
       A.st->last_cands = tot[2];
       A.st->last_fallback = tot[3];
       A.st->last_stays = tot[5];
+      A.st->last_pstays = tot[6];
       A.st->last_tiles = (unsigned long long)A.n_tiles;
       if (t >= 0 && tot[4] > 0) {
         A.sse_hist[t] = tsse;
@@ -136,6 +138,8 @@ __global__ void k_reset_run(DevState* st, CloudRun* crun, CloudAcc* cacc, int B)
   if (b >= B) return;
   crun[b].done = 0;
   crun[b].passes = 0;
+  crun[b].dmax[0] = 0u;
+  crun[b].dmax[1] = 0u;
   crun[b].last_changed = 0;
   crun[b].last_sse = 0.0;
   crun[b].final_sse = 0.0;
@@ -177,11 +181,26 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
     A.acc[j] = Acc{{0ull, 0ull, 0ull}, 0ull};
     long long cnt = (long long)a.cnt;
     if (counts_out) counts_out[j] = (int32_t)cnt;
+    const float4 c_old = c;
     if (cnt > 0) {
       const double u = exp2(-(double)A.crun[b].s_glob) / (double)cnt;
       c.x = (float)((double)c.x + (double)(long long)a.s[0] * u);
       c.y = (float)((double)c.y + (double)(long long)a.s[1] * u);
       if (d == 3) c.z = (float)((double)c.z + (double)(long long)a.s[2] * u);
+    }
+    if (A.stay && t >= 0) {
+      // the drift Delta[j] of Algorithm 1's refine step (rounded up) and
+      // the cloud's max drift, for the next inter-bound search: the
+      // maximum is taken over the warp's lanes of the same cloud first, so
+      // that one atomic per warp and cloud reaches the shared word
+      const float dx = c.x - c_old.x, dy = c.y - c_old.y, dz = c.z - c_old.z;
+      const float dl = sqrtf(dx * dx + dy * dy + dz * dz) * 1.0001f;
+      A.drift[j] = dl;
+      CloudRun& r = A.crun[b];
+      const unsigned peers = __match_any_sync(__activemask(), b);
+      const unsigned wmax = __reduce_max_sync(peers, __float_as_uint(dl));
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&r.dmax[t & 1], wmax);
+      if (j == A.clouds[b].c0) r.dmax[(t + 1) & 1] = 0u;
     }
   }
   A.cw[j] = c;
@@ -229,14 +248,30 @@ __device__ __forceinline__ long long cell_index(const Grid& G, int cx, int cy, i
   return ((long long)cz * G.dims[1] + cy) * G.dims[0] + cx;
 }
 
+// floor(a / b) for 0 <= a < 2^22 and b >= 1 by one FP32 reciprocal: the
+// error of (a + 0.5) * rn(1/b) stays below 2^-23 (a + 0.5) / b < 0.5 / b,
+// the distance of (a + 0.5) / b from the nearest integer, so the floor is
+// exact.  (Integer division by a runtime divisor is a long emulated
+// sequence.)
+__device__ __forceinline__ unsigned div_small(unsigned a, unsigned b, float rb) {
+  return (unsigned)__fmul_rn((float)a + 0.5f, rb);
+}
+
 // q-th cell (x fastest) of an nx x ny x nz range; q < 2^31 (the cell paths
 // only run for ranges below the flat-scan threshold), so 32-bit division
-// suffices -- 64-bit division is emulated and far slower.
+// suffices -- 64-bit division is emulated and far slower; below 2^22 cells
+// the reciprocal form above replaces it.
 __device__ __forceinline__ void decode_cell(long long q, int nx, int ny, int& dx, int& dy, int& dz) {
   const unsigned uq = (unsigned)q;
-  const unsigned r = uq / (unsigned)nx;
+  unsigned r, z;
+  if (uq < (1u << 22)) {
+    r = div_small(uq, (unsigned)nx, __frcp_rn((float)nx));
+    z = div_small(r, (unsigned)ny, __frcp_rn((float)ny));
+  } else {
+    r = uq / (unsigned)nx;
+    z = r / (unsigned)ny;
+  }
   dx = (int)(uq - r * (unsigned)nx);
-  const unsigned z = r / (unsigned)ny;
   dy = (int)(r - z * (unsigned)ny);
   dz = (int)z;
 }
@@ -410,41 +445,71 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
       count += __popc(bal);
     }
   } else {
+    // The range's cells, 32 per round, one per lane; their bucket entries
+    // are then taken 32 at a time across the lanes (each lane finds the
+    // cell that holds its entry by a binary search over the cells'
+    // exclusive count prefix), so a round costs ceil(entries / 32) tests
+    // instead of the fullest cell's count.
+    bool any_ovf = false;   // a cell of the range overflowed into the list
     for (long long q0 = 0; q0 < ncell; q0 += 32) {
-      long long q = q0 + lane;
+      const long long q = q0 + lane;
       long long cell = 0;
       int cnt = 0;
       if (q < ncell) {
         int ox, oy, oz;
         decode_cell(q, nx, ny, ox, oy, oz);
         cell = cell_index(G, rlo[0] + ox, rlo[1] + oy, rlo[2] + oz);
-        cnt = min(gcnt[cell], kBucketCap);
+        const int raw = gcnt[cell];
+        any_ovf = any_ovf || raw > kBucketCap;
+        cnt = min(raw, kBucketCap);
       }
-      const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-      for (int i = 0; i < cmax; ++i) {
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int excl = incl - cnt;
+      for (int j0 = 0; j0 < total; j0 += 32) {
+        const int j = j0 + lane;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int e = __shfl_sync(0xffffffffu, excl, L + step);
+          if (e <= j) L += step;
+        }
+        const long long cl = __shfl_sync(0xffffffffu, cell, L);
+        const int slot = j - __shfl_sync(0xffffffffu, excl, L);
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < cnt) e = gbkt[cell * kBucketCap + i];
-        const bool keep = i < cnt && mind2(lo, hi, e.x, e.y, e.z, d) <= u2k &&
-                          !dominated(lo, hi, r1, slack, e.x, e.y, e.z, d);
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        int pos = count + __popc(bal & lt);
+        bool keep = false;
+        if (j < total) {
+          e = gbkt[cl * kBucketCap + slot];
+          keep = mind2(lo, hi, e.x, e.y, e.z, d) <= u2k &&
+                 !dominated(lo, hi, r1, slack, e.x, e.y, e.z, d);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = count + __popc(bal & lt);
         if (keep && pos < kTileCap) out[pos] = e;
         count += __popc(bal);
       }
     }
-    for (int q0 = 0; q0 < n_ovf; q0 += 32) {
-      int q = q0 + lane;
-      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-      bool keep = false;
-      if (q < n_ovf) {
-        c = ovf[q];
-        keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k &&
-               !dominated(lo, hi, r1, slack, c.x, c.y, c.z, d);
+    // overflow entries live only in cells counted above kBucketCap
+    if (__any_sync(0xffffffffu, any_ovf)) {
+      for (int q0 = 0; q0 < n_ovf; q0 += 32) {
+        int q = q0 + lane;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool keep = false;
+        if (q < n_ovf) {
+          c = ovf[q];
+          keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k &&
+                 !dominated(lo, hi, r1, slack, c.x, c.y, c.z, d);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int pos = count + __popc(bal & lt);
+        if (keep && pos < kTileCap) out[pos] = c;
+        count += __popc(bal);
       }
-      unsigned bal = __ballot_sync(0xffffffffu, keep);
-      int pos = count + __popc(bal & lt);
-      if (keep && pos < kTileCap) out[pos] = c;
-      count += __popc(bal);
     }
   }
   if (lane == 0) {
@@ -601,21 +666,6 @@ __device__ __forceinline__ int filter_box(const float4* __restrict__ s_c, int m,
   return cnt;
 }
 
-__device__ __forceinline__ void add_group(const IterArgs& A, int D, int L, int sx, int sy, int sz,
-                                          int cnt, int s_q, int s_glob) {
-  Acc* a = &A.acc[L];
-  red_add_u64(&a->s[0], (unsigned long long)rescale(sx, s_q, s_glob));
-  red_add_u64(&a->s[1], (unsigned long long)rescale(sy, s_q, s_glob));
-  if (D == 3) red_add_u64(&a->s[2], (unsigned long long)rescale(sz, s_q, s_glob));
-  red_add_u64(&a->cnt, (unsigned long long)cnt);
-}
-
-// unit exponent s with n_max * max|r| * 2^s < 2^31 for groups of up to
-// 2^(31 - 1 - bits) points: 2^bits * max|r| * 2^s < 2^30
-__device__ __forceinline__ int group_scale(float m, int bits) {
-  return m > 0.f ? min(bits - exp_bound(m), 127) : 0;
-}
-
 // The entries of src[0..m) (global memory) that can hold the nearest
 // centroid of some point inside [lo, hi], written compactly to out (shared
 // memory, m <= kTileCap); returns the count.  U = min over the list of
@@ -623,7 +673,7 @@ __device__ __forceinline__ int group_scale(float m, int bits) {
 // cloud does), and a point's nearest centroid c* has mind(box, c*) <= U.
 template <int D>
 __device__ __forceinline__ int filter_list(const float4* __restrict__ src, int m, float4 lo,
-                                           float4 hi, float4* __restrict__ out) {
+                                           float4 hi, float4* __restrict__ out, bool slot_keys) {
   const int lane = threadIdx.x & 31;
   float u = INFINITY;
   for (int j = lane; j < m; j += 32) {
@@ -642,101 +692,318 @@ __device__ __forceinline__ int filter_list(const float4* __restrict__ src, int m
       keep = mind2(lo, hi, c.x, c.y, c.z, D) <= u2k;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) out[cnt + __popc(bal & lt)] = c;
+    const int pos = cnt + __popc(bal & lt);
+    if (slot_keys) c.w = __int_as_float((__float_as_int(c.w) << 8) | pos);
+    if (keep) out[pos] = c;
     cnt += __popc(bal);
   }
   __syncwarp();
   return cnt;
 }
 
-// Tile epilogue shared by k_assign and k_accum_labels: residuals p - c of
-// the tile's points (4 rows x 2 per lane) against their own centroid, in
-// 32-bit fixed point with one tile-wide power-of-two scale (256 points *
-// max|r| * 2^s < 2^31, so int32 sums cannot overflow), summed per label
-// and added to the per-centroid accumulators with 64-bit integer atomics.
-// A tile whose points all share one label loads its centroid once and adds
-// one group; otherwise every point loads its own centroid and the labels
-// are taken one at a time (the smallest pending label of the warp).  The
-// sums depend only on the tile and the labels, so every caller gets the
-// same sums bit for bit.  Returns the tile's label when all its points
-// share one, else -1.
+// ---------------------------------------------------------------------------
+// Update sums of one tile (the refine step's sv(j) of Algorithm 1, in exact
+// integer arithmetic).  Each point's residual r = p - c_label (FP32, the
+// same p + (-c) as the distance) is scaled by one tile-wide power of two
+// 2^s and rounded to an integer q; the q of a label's points are summed in
+// int32 across the warp and added, rescaled to the cloud's unit 2^-s_glob,
+// to that centroid's 64-bit accumulators with integer atomics.  Integer
+// addition is exact and order independent, so the centroids do not depend
+// on the order of the atomics.
+//
+// Scale: every |r_axis| <= sqrt(max d^2) < 2^ceil(e2/2) with max d^2 <
+// 2^e2 over the tile's points, so s = 22 - ceil(e2/2) keeps |r * 2^s| below
+// 2^22 and a 256-point sum below 2^30.  Rounding: fma(r, 2^s, 1.5 * 2^23)
+// leaves round-to-nearest-even(r * 2^s) in the low bits of the float
+// (exact while |r * 2^s| <= 2^22); the raw bit patterns are summed with
+// wrap-around and the 0x4B400000 offset of the cnt summands is taken off
+// once per group.
+//
+// Every caller (k_assign's list and global paths, k_accum_labels for
+// caller-given labels) passes the same residuals and squared norms for the
+// same labels, so the sums agree bit for bit whatever grouping it uses.
+// ---------------------------------------------------------------------------
+constexpr int kPts = 2 * kRowsPerWarp;      // points per lane
+constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23
+constexpr unsigned kMagicBits = 0x4B400000u;
+
+__device__ __forceinline__ int residual_scale(float m2) {
+  if (!(m2 > 0.f)) return 0;
+  const int e2 = exp_bound(m2);
+  return min(22 - ((e2 + 1) >> 1), 127);
+}
+
+__device__ __forceinline__ void add_group(const IterArgs& A, int D, int L, int sx, int sy, int sz,
+                                          int cnt, int s_q, int s_glob) {
+  Acc* a = &A.acc[L];
+  red_add_u64(&a->s[0], (unsigned long long)rescale(sx, s_q, s_glob));
+  red_add_u64(&a->s[1], (unsigned long long)rescale(sy, s_q, s_glob));
+  if (D == 3) red_add_u64(&a->s[2], (unsigned long long)rescale(sz, s_q, s_glob));
+  red_add_u64(&a->cnt, (unsigned long long)cnt);
+}
+
+// q(r) = the raw float bits of fma(r, 2^s, 1.5 * 2^23): round(r * 2^s) +
+// 0x4B400000 for |r * 2^s| <= 2^22.
+__device__ __forceinline__ unsigned quantize(float r, float scl) {
+  return __float_as_uint(__fmaf_rn(r, scl, kMagic));
+}
+
+// Groups are keyed by g: the label itself, or (slots) the candidate-list
+// position whose entry sc[g] carries (label << 8 | g) in .w.  q*: the
+// quantized residuals (quantize) at scale 2^s_t.  With mask_keys every key
+// is below 32 and the distinct keys are taken from one warp-wide bit mask;
+// otherwise the smallest pending key is taken in turn.  Returns the tile's
+// label when all its points share one, else -1.
 template <int D>
-__device__ __forceinline__ int accumulate_tile(const IterArgs& A, const float2 (&px)[kRowsPerWarp],
-                                                const float2 (&py)[kRowsPerWarp],
-                                                const float2 (&pz)[kRowsPerWarp],
-                                                const int2 (&lab)[kRowsPerWarp],
-                                                const bool (&va)[kRowsPerWarp],
-                                                const bool (&vb)[kRowsPerWarp], int s_glob) {
-  constexpr int H = 2 * kRowsPerWarp;
+__device__ __forceinline__ int tile_sums(const IterArgs& A, const unsigned (&qx)[kPts],
+                                         const unsigned (&qy)[kPts], const unsigned (&qz)[kPts],
+                                         const int (&g)[kPts], const bool (&pv)[kPts], int s_t,
+                                         bool slots, bool mask_keys,
+                                         const float4* __restrict__ sc, int s_glob) {
   const int lane = threadIdx.x & 31;
-  int lb[H];
-  bool pend[H];
-  int lmin = INT_MAX;
+  auto label_of = [&](int key) { return slots ? (__float_as_int(sc[key].w) >> 8) : key; };
+  auto flush = [&](int key, bool all) {
+    unsigned sx = 0, sy = 0, sz = 0, cnt = 0;
+#pragma unroll
+    for (int h = 0; h < kPts; ++h) {
+      const bool in = pv[h] && (all || g[h] == key);
+      sx += in ? qx[h] : 0u;
+      sy += in ? qy[h] : 0u;
+      if (D == 3) sz += in ? qz[h] : 0u;
+      cnt += in ? 1u : 0u;
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    sx = __reduce_add_sync(0xffffffffu, sx) - cnt * kMagicBits;
+    sy = __reduce_add_sync(0xffffffffu, sy) - cnt * kMagicBits;
+    if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz) - cnt * kMagicBits;
+    if (lane == 0)
+      add_group(A, D, label_of(key), (int)sx, (int)sy, (int)sz, (int)cnt, s_t, s_glob);
+  };
+  if (mask_keys) {
+    unsigned m = 0;
+#pragma unroll
+    for (int h = 0; h < kPts; ++h) m |= pv[h] ? (1u << g[h]) : 0u;
+    m = __reduce_or_sync(0xffffffffu, m);
+    if (m == 0) return -1;
+    if ((m & (m - 1)) == 0) {   // one group: every valid point
+      const int key = __ffs(m) - 1;
+      flush(key, true);
+      return label_of(key);
+    }
+    while (m) {
+      const int key = __ffs(m) - 1;
+      m &= m - 1;
+      flush(key, false);
+    }
+    return -1;
+  }
+  int lmin = INT_MAX, lmax = INT_MIN;
+#pragma unroll
+  for (int h = 0; h < kPts; ++h) {
+    lmin = pv[h] ? min(lmin, g[h]) : lmin;
+    lmax = pv[h] ? max(lmax, g[h]) : lmax;
+  }
+  int key = __reduce_min_sync(0xffffffffu, lmin);
+  if (key == INT_MAX) return -1;
+  if (__reduce_max_sync(0xffffffffu, lmax) == key) {   // one group
+    flush(key, true);
+    return label_of(key);
+  }
+  while (key != INT_MAX) {
+    flush(key, false);
+    lmin = INT_MAX;
+#pragma unroll
+    for (int h = 0; h < kPts; ++h) lmin = (pv[h] && g[h] > key) ? min(lmin, g[h]) : lmin;
+    key = __reduce_min_sync(0xffffffffu, lmin);
+  }
+  return -1;
+}
+
+// The same sums for a tile whose points are keyed by candidate-list
+// position (sc[g].w = label << 8 | g): each group reads its centroid once
+// from shared memory and quantizes its points' residuals on the fly, so no
+// per-point residual is kept in registers.  The residual and its rounding
+// are those of quantize(p + (-c)), as in every other caller.
+template <int D>
+__device__ __forceinline__ int tile_sums_slots(const IterArgs& A, const Pts<D>& P,
+                                               const unsigned (&gs)[2], unsigned pm, int s_t,
+                                               int q, const float4* __restrict__ sc, int s_glob) {
+  // gs: the points' list positions, one byte each (point h in byte h & 3 of
+  // gs[h >> 2]); pm: bit h set for a valid point h
+  const int lane = threadIdx.x & 31;
+  const float scl = pow2f(s_t);
+  auto slot = [&](int h) { return (int)((gs[h >> 2] >> (8 * (h & 3))) & 0xffu); };
+  auto flush = [&](int key, bool all) {
+    const float4 c = sc[key];
+    unsigned sx = 0, sy = 0, sz = 0, cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int h = 2 * r + hh;
+        const bool in = ((pm >> h) & 1u) && (all || slot(h) == key);
+        const unsigned ux = quantize(__fadd_rn(hh ? P.x[r].y : P.x[r].x, -c.x), scl);
+        const unsigned uy = quantize(__fadd_rn(hh ? P.y[r].y : P.y[r].x, -c.y), scl);
+        sx += in ? ux : 0u;
+        sy += in ? uy : 0u;
+        if (D == 3) {
+          const unsigned uz = quantize(__fadd_rn(hh ? P.z[r].y : P.z[r].x, -c.z), scl);
+          sz += in ? uz : 0u;
+        }
+        cnt += in ? 1u : 0u;
+      }
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    sx = __reduce_add_sync(0xffffffffu, sx) - cnt * kMagicBits;
+    sy = __reduce_add_sync(0xffffffffu, sy) - cnt * kMagicBits;
+    if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz) - cnt * kMagicBits;
+    if (lane == 0)
+      add_group(A, D, __float_as_int(c.w) >> 8, (int)sx, (int)sy, (int)sz, (int)cnt, s_t, s_glob);
+    return __float_as_int(c.w) >> 8;
+  };
+  if (q <= 32) {
+    unsigned m = 0;
+#pragma unroll
+    for (int h = 0; h < kPts; ++h) m |= ((pm >> h) & 1u) ? (1u << slot(h)) : 0u;
+    m = __reduce_or_sync(0xffffffffu, m);
+    if (m == 0) return -1;
+    if ((m & (m - 1)) == 0) return flush(__ffs(m) - 1, true);   // one group
+    while (m) {
+      const int key = __ffs(m) - 1;
+      m &= m - 1;
+      flush(key, false);
+    }
+    return -1;
+  }
+  int lmin = INT_MAX, lmax = INT_MIN;
+#pragma unroll
+  for (int h = 0; h < kPts; ++h) {
+    const bool v = (pm >> h) & 1u;
+    lmin = v ? min(lmin, slot(h)) : lmin;
+    lmax = v ? max(lmax, slot(h)) : lmax;
+  }
+  int key = __reduce_min_sync(0xffffffffu, lmin);
+  if (key == INT_MAX) return -1;
+  if (__reduce_max_sync(0xffffffffu, lmax) == key) return flush(key, true);
+  while (key != INT_MAX) {
+    flush(key, false);
+    lmin = INT_MAX;
+#pragma unroll
+    for (int h = 0; h < kPts; ++h)
+      lmin = (((pm >> h) & 1u) && slot(h) > key) ? min(lmin, slot(h)) : lmin;
+    key = __reduce_min_sync(0xffffffffu, lmin);
+  }
+  return -1;
+}
+
+// The same sums, row by row, for a tile whose staged list has at most 32
+// entries (keys are list positions < 32).  Each point quantizes its residual
+// to its own staged centroid once; every row (64 points) then adds each of
+// its groups to a per-warp shared-memory accumulator of that list position
+// (one writer, lane 0, so no atomics), and the warp's lanes flush the
+// positions that received points to the global accumulators together.
+// Rows hold fewer distinct labels than whole tiles, so each point is
+// visited by fewer groups.  Int32 accumulation cannot overflow: a tile's
+// points sum below 2^30 per axis (residual_scale).  Returns the tile's
+// label when all its points share one, else -1.
+template <int D>
+__device__ __forceinline__ int tile_sums_rows(const IterArgs& A, const Pts<D>& P,
+                                              const int2 (&bid)[kRowsPerWarp],
+                                              const bool (&va)[kRowsPerWarp],
+                                              const bool (&vb)[kRowsPerWarp],
+                                              const int (&nv_row)[kRowsPerWarp], int s_t, int q,
+                                              const float4* __restrict__ sc,
+                                              int4* __restrict__ sacc, int s_glob) {
+  const int lane = threadIdx.x & 31;
+  const float scl = pow2f(s_t);
+  if (lane < q) sacc[lane] = make_int4(0, 0, 0, 0);
+  __syncwarp();
+  unsigned tile_mask = 0;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    lb[2 * r] = lab[r].x;
-    lb[2 * r + 1] = lab[r].y;
-    pend[2 * r] = va[r];
-    pend[2 * r + 1] = vb[r];
+    if (nv_row[r] == 0) continue;   // warp-uniform
+    const int ga = bid[r].x & 255, gb = bid[r].y & 255;
+    const float4 ca = sc[ga], cb = sc[gb];
+    const unsigned ax = quantize(__fadd_rn(P.x[r].x, -ca.x), scl);
+    const unsigned ay = quantize(__fadd_rn(P.y[r].x, -ca.y), scl);
+    const unsigned az = D == 3 ? quantize(__fadd_rn(P.z[r].x, -ca.z), scl) : kMagicBits;
+    const unsigned bx = quantize(__fadd_rn(P.x[r].y, -cb.x), scl);
+    const unsigned by = quantize(__fadd_rn(P.y[r].y, -cb.y), scl);
+    const unsigned bz = D == 3 ? quantize(__fadd_rn(P.z[r].y, -cb.z), scl) : kMagicBits;
+    unsigned m = (va[r] ? 1u << ga : 0u) | (vb[r] ? 1u << gb : 0u);
+    m = __reduce_or_sync(0xffffffffu, m);
+    tile_mask |= m;
+    while (m) {
+      const int key = __ffs(m) - 1;
+      m &= m - 1;
+      const bool ia = va[r] && ga == key, ib = vb[r] && gb == key;
+      unsigned sx = (ia ? ax : 0u) + (ib ? bx : 0u);
+      unsigned sy = (ia ? ay : 0u) + (ib ? by : 0u);
+      unsigned sz = (ia ? az : 0u) + (ib ? bz : 0u);
+      const unsigned cnt = __reduce_add_sync(0xffffffffu, (unsigned)ia + (unsigned)ib);
+      sx = __reduce_add_sync(0xffffffffu, sx) - cnt * kMagicBits;
+      sy = __reduce_add_sync(0xffffffffu, sy) - cnt * kMagicBits;
+      if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz) - cnt * kMagicBits;
+      if (lane == 0) {
+        int4 a = sacc[key];
+        a.x += (int)sx;
+        a.y += (int)sy;
+        a.z += (int)sz;
+        a.w += (int)cnt;
+        sacc[key] = a;
+      }
+    }
   }
-#pragma unroll
-  for (int h = 0; h < H; ++h) lmin = pend[h] ? min(lmin, lb[h]) : lmin;
-  int L = __reduce_min_sync(0xffffffffu, lmin);
-  if (L == INT_MAX) return -1;   // no valid point
-  bool same = true;
-#pragma unroll
-  for (int h = 0; h < H; ++h) same = same && (!pend[h] || lb[h] == L);
-  const bool single = __all_sync(0xffffffffu, same);
-  float rx[H], ry[H], rz[H];
-  float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (single) c0 = __ldg(&A.cw[L]);
-  float ml = 0.f;
+  __syncwarp();
+  if (lane < q) {
+    const int4 a = sacc[lane];
+    if (a.w > 0)
+      add_group(A, D, __float_as_int(sc[lane].w) >> 8, a.x, a.y, a.z, a.w, s_t, s_glob);
+  }
+  if (tile_mask != 0 && (tile_mask & (tile_mask - 1)) == 0)
+    return __float_as_int(sc[__ffs(tile_mask) - 1].w) >> 8;
+  return -1;
+}
+
+// Quantized residuals of a tile's points against their labels' centroids
+// read from the working centroids (global memory); returns the scale
+// exponent s_t (residual_scale of the tile's max squared residual norm).
+template <int D>
+__device__ __forceinline__ int residuals_global(const IterArgs& A,
+                                                const float2 (&px)[kRowsPerWarp],
+                                                const float2 (&py)[kRowsPerWarp],
+                                                const float2 (&pz)[kRowsPerWarp],
+                                                const int (&lb)[kPts], const bool (&pv)[kPts],
+                                                unsigned (&qx)[kPts], unsigned (&qy)[kPts],
+                                                unsigned (&qz)[kPts]) {
+  float rx[kPts], ry[kPts], rz[kPts];
+  float m2 = 0.f;
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int h = 2 * r + hh;
       rx[h] = ry[h] = rz[h] = 0.f;
-      if (pend[h]) {
-        const float4 c = single ? c0 : __ldg(&A.cw[lb[h]]);
+      if (pv[h]) {
+        const float4 c = __ldg(&A.cw[lb[h]]);
         rx[h] = __fadd_rn(hh ? px[r].y : px[r].x, -c.x);
         ry[h] = __fadd_rn(hh ? py[r].y : py[r].x, -c.y);
         if (D == 3) rz[h] = __fadd_rn(hh ? pz[r].y : pz[r].x, -c.z);
+        float d2 = __fmaf_rn(ry[h], ry[h], __fmul_rn(rx[h], rx[h]));
+        if (D == 3) d2 = __fmaf_rn(rz[h], rz[h], d2);
+        m2 = fmaxf(m2, d2);
       }
-      ml = fmaxf(ml, fmaxf(fmaxf(fabsf(rx[h]), fabsf(ry[h])), fabsf(rz[h])));
     }
   }
-  const int s_t = group_scale(warp_max_nonneg(ml), 22);
-  const float sc = pow2f(s_t);
-  int qx[H], qy[H], qz[H];
+  const int s_t = residual_scale(warp_max_nonneg(m2));
+  const float scl = pow2f(s_t);
 #pragma unroll
-  for (int h = 0; h < H; ++h) {
-    qx[h] = __float2int_rn(rx[h] * sc);
-    qy[h] = __float2int_rn(ry[h] * sc);
-    qz[h] = D == 3 ? __float2int_rn(rz[h] * sc) : 0;
+  for (int h = 0; h < kPts; ++h) {
+    qx[h] = quantize(rx[h], scl);
+    qy[h] = quantize(ry[h], scl);
+    qz[h] = quantize(rz[h], scl);
   }
-  while (true) {
-    int sx = 0, sy = 0, sz = 0, cnt = 0;
-    lmin = INT_MAX;
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-      const bool g = pend[h] && lb[h] == L;
-      sx += g ? qx[h] : 0;
-      sy += g ? qy[h] : 0;
-      sz += g ? qz[h] : 0;
-      cnt += g ? 1 : 0;
-      pend[h] = pend[h] && !g;
-      lmin = pend[h] ? min(lmin, lb[h]) : lmin;
-    }
-    sx = __reduce_add_sync(0xffffffffu, sx);
-    sy = __reduce_add_sync(0xffffffffu, sy);
-    if (D == 3) sz = __reduce_add_sync(0xffffffffu, sz);
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if (lane == 0) add_group(A, D, L, sx, sy, sz, cnt, s_t, s_glob);
-    if (single) return L;
-    L = __reduce_min_sync(0xffffffffu, lmin);
-    if (L == INT_MAX) return -1;
-  }
+  return s_t;
 }
 
 // Tile SSE in fixed point (unit 2^-s_sse) with one tile-wide scale
@@ -781,10 +1048,10 @@ __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t ba
 // Assignment of tile t (one warp) from its search unit's candidate list:
 // labels, SSE and the update sums.  sc / sr / slbw: the warp's shared
 // staging (kTileCap candidates, kTileCap indices, 32 bounds).
-template <int D, bool BRUTE, bool MULTI, bool UNITS>
+template <int D, bool BRUTE, bool MULTI, bool UNITS, bool PSTAY>
 __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __restrict__ sc,
                                             unsigned short* __restrict__ sr,
-                                            float* __restrict__ slbw) {
+                                            float* __restrict__ slbw, int4* __restrict__ sacc) {
   const int lane = threadIdx.x & 31;
   const int b = MULTI ? A.tcloud[t] : 0;
   if (MULTI && A.crun[b].done) return;
@@ -811,6 +1078,15 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
     bid[r] = make_int2(0, 0);
   }
   unsigned long long evals = 0;   // point x candidate evaluations of this warp
+  bool slots = false;             // candidate keys carry list positions (see below)
+  int q_tile = 0;                 // length of the staged list
+  // point stay test (stay == 2): per point its kept label (or -1) and its
+  // squared distance; rows whose valid points all stay
+  int sl[kPts];
+  float sd[kPts];
+  unsigned row_stay = 0u;
+  int n_pstay = 0;
+  bool any_pstay = false;
   if (BRUTE) {
     for (int j0 = c0; j0 < c1; j0 += kTileCap) {
       const int m = min(kTileCap, c1 - j0);
@@ -826,16 +1102,75 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
     if (qs == 0 && lane == 0) atomicOr(&A.st->err, kErrEmptyList);
     if (qs <= kTileCap) {
       const float4* __restrict__ src = A.tlist + (int64_t)u * kTileCap;
+      // Staged entries carry (id << 8 | list position) in .w when ids fit
+      // 24 bits: the (d^2, key) order is the (d^2, id) order, and the
+      // winner's position finds its centroid in shared memory for the
+      // update sums.
+      slots = A.slot_keys != 0;
       int q = qs;
       if (UNITS) {
         // the unit's list holds every candidate of the group's box; narrow
         // it with this tile's own box (the bound of k_search)
-        q = filter_list<D>(src, qs, A.tbox[2 * t], A.tbox[2 * t + 1], sc);
+        q = filter_list<D>(src, qs, A.tbox[2 * t], A.tbox[2 * t + 1], sc, slots);
       } else {
-        for (int i = lane; i < qs; i += 32) sc[i] = src[i];
+        for (int i = lane; i < qs; i += 32) {
+          float4 c = src[i];
+          if (slots) c.w = __int_as_float((__float_as_int(c.w) << 8) | i);
+          sc[i] = c;
+        }
         __syncwarp();
       }
-      if (q <= A.sort_max) {   // sort_max <= 32
+      q_tile = q;
+      if (PSTAY) {
+        // The point test of the bound layer (Eq. interbound1; the leaf
+        // branch of Algorithm 1's Assign): a point within cb[a]/2 of its
+        // last centroid c_a still has c_a as its unique nearest centroid.
+        // Rows whose points all pass skip the candidate loop.
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r) {
+          bool ok[2];
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int h = 2 * r + hh;
+            const bool v = hh ? vb[r] : va[r];
+            ok[hh] = !v;
+            sl[h] = -1;
+            if (v) {
+              const int a = A.lab[base + r * kRowPts + 2 * lane + hh];
+              if (a >= c0 && a < c1) {
+                const float4 c = __ldg(&A.cw[a]);
+                const float dx = __fadd_rn(hh ? P.x[r].y : P.x[r].x, -c.x);
+                const float dy = __fadd_rn(hh ? P.y[r].y : P.y[r].x, -c.y);
+                float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+                if (D == 3) {
+                  const float dz = __fadd_rn(hh ? P.z[r].y : P.z[r].x, -c.z);
+                  d2 = __fmaf_rn(dz, dz, d2);
+                }
+                if (d2 <= kStay * __ldg(&A.cb2[a])) {
+                  sl[h] = a;
+                  sd[h] = d2;
+                  ok[hh] = true;
+                  ++n_pstay;
+                }
+              }
+            }
+          }
+          if (__all_sync(0xffffffffu, ok[0] && ok[1])) row_stay |= 1u << r;
+        }
+        any_pstay = __any_sync(0xffffffffu, n_pstay > 0);
+      }
+      if (PSTAY && row_stay == 0xfu) {
+        // every point keeps its label: no candidate is evaluated
+      } else if (PSTAY && row_stay != 0u) {
+        for (int i = lane; i < q; i += 32) sr[i] = (unsigned short)i;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r) {
+          if (nv_row[r] == 0 || ((row_stay >> r) & 1u)) continue;   // warp-uniform
+          eval_row<D>(sc, sr, q, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
+          evals += (unsigned long long)q * nv_row[r];
+        }
+      } else if (q <= A.sort_max) {   // sort_max <= 32
         // Short list: order it by the lower bound mind^2(tile box, c) and
         // stop once the next bound exceeds every point's current best (the
         // kNN pruning rule of Algorithm 1's kNN function, with the tile box
@@ -926,55 +1261,104 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
   const int s_glob = A.crun[b].s_glob, s_sse = A.crun[b].s_sse;
   long long sse = 0;
   int changed = 0;
+  int lb[kPts], gk[kPts];   // label (context-wide id) and group key of each point
+  bool pv[kPts];
+  float m2 = 0.f;           // max squared distance of the lane's valid points
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    const int ka = bid[r].x, kb = bid[r].y;
+    lb[2 * r] = slots ? ka >> 8 : ka;
+    lb[2 * r + 1] = slots ? kb >> 8 : kb;
+    if (PSTAY && any_pstay) {   // points that kept their label: theirs, with its distance
+      if (sl[2 * r] >= 0) {
+        lb[2 * r] = sl[2 * r];
+        best[r].x = sd[2 * r];
+      }
+      if (sl[2 * r + 1] >= 0) {
+        lb[2 * r + 1] = sl[2 * r + 1];
+        best[r].y = sd[2 * r + 1];
+      }
+    }
+    gk[2 * r] = slots ? ka & 255 : lb[2 * r];
+    gk[2 * r + 1] = slots ? kb & 255 : lb[2 * r + 1];
+    pv[2 * r] = va[r];
+    pv[2 * r + 1] = vb[r];
+    m2 = fmaxf(m2, fmaxf(va[r] ? best[r].x : 0.f, vb[r] ? best[r].y : 0.f));
+  }
+  if (PSTAY && any_pstay) slots = false;   // the kept labels carry no list position
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
     if (nv_row[r] == 0) continue;   // warp-uniform
     const int64_t i = base + r * kRowPts + 2 * lane;
-    const int la = bid[r].x, lb = bid[r].y;
+    const int la = lb[2 * r], lc = lb[2 * r + 1];
     if (A.track_changes) {
-      int pa = va[r] ? A.lab[i] : la, pb = vb[r] ? A.lab[i + 1] : lb;
-      changed += (int)(pa != la) + (int)(pb != lb);
+      int pa = va[r] ? A.lab[i] : la, pb = vb[r] ? A.lab[i + 1] : lc;
+      changed += (int)(pa != la) + (int)(pb != lc);
     }
     if (va[r] && vb[r]) {
-      *reinterpret_cast<int2*>(A.lab + i) = make_int2(la, lb);
+      *reinterpret_cast<int2*>(A.lab + i) = make_int2(la, lc);
     } else if (va[r]) {
       A.lab[i] = la;
     } else if (vb[r]) {
-      A.lab[i + 1] = lb;
+      A.lab[i + 1] = lc;
     }
   }
   if (A.want_sse) sse = tile_sse(best, va, vb, s_sse);
-  const int single = accumulate_tile<D>(A, P.x, P.y, P.z, bid, va, vb, s_glob);
+  int single;
+  if (slots) {
+    // the tile's max squared residual norm is its max best d^2
+    const int s_t = residual_scale(warp_max_nonneg(m2));
+    if (q_tile <= 32) {
+      single = tile_sums_rows<D>(A, P, bid, va, vb, nv_row, s_t, q_tile, sc, sacc, s_glob);
+    } else {
+      unsigned gs[2] = {0u, 0u}, pm = 0u;
+#pragma unroll
+      for (int h = 0; h < kPts; ++h) {
+        gs[h >> 2] |= (unsigned)gk[h] << (8 * (h & 3));
+        pm |= pv[h] ? (1u << h) : 0u;
+      }
+      single = tile_sums_slots<D>(A, P, gs, pm, s_t, q_tile, sc, s_glob);
+    }
+  } else {
+    unsigned qx[kPts], qy[kPts], qz[kPts];
+    const int s_t = residuals_global<D>(A, P.x, P.y, P.z, lb, pv, qx, qy, qz);
+    single = tile_sums<D>(A, qx, qy, qz, lb, pv, s_t, false, false, sc, s_glob);
+  }
   changed = __reduce_add_sync(0xffffffffu, changed);
   if (lane == 0) {
     if (A.stay) A.tlab[t] = single;
     CloudAcc& ca = A.cacc[b];
-    red_add_u64(&ca.sse[t & (kCloudSlots - 1)], (unsigned long long)sse);
+    if (sse) red_add_u64(&ca.sse[t & (kCloudSlots - 1)], (unsigned long long)sse);
     if (changed) red_add_u64(&ca.changed[t & (kCloudSlots - 1)], (unsigned long long)changed);
     if (A.want_stats) red_add_u64(&A.slots[t & (kSlots - 1)].evals, evals);
+  }
+  if (PSTAY && A.want_stats && any_pstay) {
+    const int np = __reduce_add_sync(0xffffffffu, n_pstay);
+    if (lane == 0) red_add_u64(&A.slots[t & (kSlots - 1)].pstays, (unsigned long long)np);
   }
 }
 
 
 // UNITS: tiles share search units (tile_group > 1) and filter their unit's
-// list with their own box.
-template <int D, bool BRUTE, bool MULTI, bool UNITS>
+// list with their own box.  PSTAY: the point stay test of the bound layer.
+template <int D, bool BRUTE, bool MULTI, bool UNITS, bool PSTAY>
 __global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAssignWarps)
     k_assign(const __grid_constant__ IterArgs A) {
   __shared__ float4 s_c[kAssignWarps][kTileCap];
   __shared__ unsigned short s_r[kAssignWarps][kTileCap];
   __shared__ float slb[kAssignWarps][32];
+  __shared__ int4 s_acc[kAssignWarps][32];
   if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
   const int w = threadIdx.x >> 5;
   const int t = blockIdx.x * kAssignWarps + w;
   if (t >= A.n_tiles) return;   // warp-level exits, no CTA barrier below
-  assign_tile<D, BRUTE, MULTI, UNITS>(A, t, s_c[w], s_r[w], slb[w]);
+  assign_tile<D, BRUTE, MULTI, UNITS, PSTAY>(A, t, s_c[w], s_r[w], slb[w], s_acc[w]);
 }
 
 // ---------------------------------------------------------------------------
 // k_accum_labels: residual sums for a caller-given labelling (dkm_update;
-// cloud-local labels).  One warp per tile, grouped exactly like k_assign,
-// so both produce the same sums bit for bit for the same labels.
+// cloud-local labels).  One warp per tile with k_assign's per-tile scale, so
+// both produce the same sums bit for bit for the same labels.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
@@ -991,19 +1375,22 @@ __global__ void __launch_bounds__(kBlockThreads) k_accum_labels(IterArgs A,
   bool va[kRowsPerWarp], vb[kRowsPerWarp];
   load_points(A, D, base, se.x, se.y, x, y, z, va, vb);
   int bad = 0;
-  int2 lab[kRowsPerWarp];
-  bool oka[kRowsPerWarp], okb[kRowsPerWarp];
+  int lab[kPts];
+  bool ok[kPts];
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
     const int64_t i = base + r * kRowPts + 2 * lane;
     const int la = va[r] ? ulab[perm[i]] : 0;
-    const int lb = vb[r] ? ulab[perm[i + 1]] : 0;
-    oka[r] = va[r] && la >= 0 && la < kb;
-    okb[r] = vb[r] && lb >= 0 && lb < kb;
-    bad |= (va[r] && !oka[r]) || (vb[r] && !okb[r]);
-    lab[r] = make_int2(c0 + (oka[r] ? la : 0), c0 + (okb[r] ? lb : 0));
+    const int lc = vb[r] ? ulab[perm[i + 1]] : 0;
+    ok[2 * r] = va[r] && la >= 0 && la < kb;
+    ok[2 * r + 1] = vb[r] && lc >= 0 && lc < kb;
+    bad |= (va[r] && !ok[2 * r]) || (vb[r] && !ok[2 * r + 1]);
+    lab[2 * r] = c0 + (ok[2 * r] ? la : 0);
+    lab[2 * r + 1] = c0 + (ok[2 * r + 1] ? lc : 0);
   }
-  accumulate_tile<D>(A, x, y, z, lab, oka, okb, A.crun[b].s_glob);
+  unsigned qx[kPts], qy[kPts], qz[kPts];
+  const int s_t = residuals_global<D>(A, x, y, z, lab, ok, qx, qy, qz);
+  tile_sums<D>(A, qx, qy, qz, lab, ok, s_t, false, false, nullptr, A.crun[b].s_glob);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&A.st->label_err, 1);
 }
 
@@ -1092,12 +1479,17 @@ template <int D, bool BRUTE>
 void assign_multi(const IterArgs& A, int g, cudaStream_t s) {
   constexpr int thr = 32 * kAssignWarps;
   if (!BRUTE && A.unit_g > 1) {
-    if (A.B > 1) k_assign<D, false, true, true><<<g, thr, 0, s>>>(A);
-    else k_assign<D, false, false, true><<<g, thr, 0, s>>>(A);
+    if (A.B > 1) k_assign<D, false, true, true, false><<<g, thr, 0, s>>>(A);
+    else k_assign<D, false, false, true, false><<<g, thr, 0, s>>>(A);
     return;
   }
-  if (A.B > 1) k_assign<D, BRUTE, true, false><<<g, thr, 0, s>>>(A);
-  else k_assign<D, BRUTE, false, false><<<g, thr, 0, s>>>(A);
+  if (!BRUTE && A.stay == 2) {
+    if (A.B > 1) k_assign<D, false, true, false, true><<<g, thr, 0, s>>>(A);
+    else k_assign<D, false, false, false, true><<<g, thr, 0, s>>>(A);
+    return;
+  }
+  if (A.B > 1) k_assign<D, BRUTE, true, false, false><<<g, thr, 0, s>>>(A);
+  else k_assign<D, BRUTE, false, false, false><<<g, thr, 0, s>>>(A);
 }
 
 cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s) {
@@ -1147,8 +1539,16 @@ cudaError_t launch_export(const float4* cw, int k, int d, float* out, cudaStream
 // least r cell edges away.  Both the bound and the final value err low
 // (slack 2^-8), so cb2 never exceeds the true squared gap by more than
 // rounding and the stay test stays conservative.
+//
+// use_ub (after an update inside a run): the search starts from the upper
+// bound of Eq. ub, ub = cb[j] + Delta[j] + max(Delta) -- c_j's previous
+// nearest neighbour is still a centroid, now at most that far -- and
+// skips every cell whose box lies farther than ub from c_j, as the kNN
+// prunes centroid nodes beyond its bound.  max(Delta) is read as the
+// cloud's largest drift (a safe bound).  If nothing lies within ub after
+// rounding, the search runs again without it.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlockThreads) k_cbound(IterArgs A, int par, int d) {
+__global__ void __launch_bounds__(kBlockThreads) k_cbound(IterArgs A, int par, int d, int use_ub) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= A.k) return;
   const int b = A.kcloud[j];
@@ -1174,40 +1574,69 @@ __global__ void __launch_bounds__(kBlockThreads) k_cbound(IterArgs A, int par, i
   const int dmax = max(max(G.dims[0], G.dims[1]), G.dims[2]);
   const float margin = 1.0f / 64.0f + (float)dmax * (1.0f / 1048576.0f);
   const long long flat_cells = (long long)(cl.k / 4) + 32;
-  for (int r = 0;; ++r) {
-    int lo[3], hi[3];
-    long long ncell = 1;
-    bool whole = true;
+  float ub = INFINITY;
+  if (use_ub && A.cb2[j] < INFINITY) {
+    const float cbp = sqrtf(A.cb2[j] * (256.0f / 255.0f));
+    const float dm = __uint_as_float(A.crun[b].dmax[(par ^ 1) & 1]);
+    ub = (cbp + A.drift[j] + dm) * 1.0001f;
+  }
+  // lower bound on the distance from c_j to any point of the cell at
+  // offsets (x, y, z) from its own cell, per axis (the faces toward c_j)
+  const float cpos[3] = {c.x, c.y, c.z};
+  auto cell_lb2 = [&](int x, int y, int z) {
+    const int o[3] = {x, y, z};
+    float s2 = 0.f;
     for (int a = 0; a < 3; ++a) {
-      lo[a] = max(cc[a] - r, 0);
-      hi[a] = min(cc[a] + r, G.dims[a] - 1);
-      whole = whole && lo[a] == 0 && hi[a] == G.dims[a] - 1;
-      ncell *= (long long)(hi[a] - lo[a] + 1);
+      if (a == 2 && d != 3) break;
+      float g = 0.f;
+      if (o[a] < cc[a]) g = cpos[a] - (G.g0[a] + (float)(o[a] + 1) * edge);
+      else if (o[a] > cc[a]) g = (G.g0[a] + (float)o[a] * edge) - cpos[a];
+      g = fmaxf(g - margin * edge, 0.f);
+      s2 += g * g;
     }
-    if (ncell > flat_cells) {   // large rings: every centroid of the cloud once
-      best = INFINITY;
-      for (int q = cl.c0; q < cl.c0 + cl.k; ++q) take(A.cw[q]);
-      break;
+    return s2;
+  };
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const float ub2 = ub * ub;
+    for (int r = 0;; ++r) {
+      int lo[3], hi[3];
+      long long ncell = 1;
+      bool whole = true;
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = max(cc[a] - r, 0);
+        hi[a] = min(cc[a] + r, G.dims[a] - 1);
+        whole = whole && lo[a] == 0 && hi[a] == G.dims[a] - 1;
+        ncell *= (long long)(hi[a] - lo[a] + 1);
+      }
+      if (ncell > flat_cells) {   // large rings: every centroid of the cloud once
+        best = INFINITY;
+        for (int q = cl.c0; q < cl.c0 + cl.k; ++q) take(A.cw[q]);
+        break;
+      }
+      // the shell of ring r (cells at Chebyshev distance exactly r)
+      for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+          for (int x = lo[0]; x <= hi[0]; ++x) {
+            const int cheb = max(max(abs(x - cc[0]), abs(y - cc[1])), abs(z - cc[2]));
+            if (cheb != r) continue;
+            if (ub < INFINITY && cell_lb2(x, y, z) > ub2) continue;   // beyond the bound
+            const long long cell = ((long long)z * G.dims[1] + y) * G.dims[0] + x;
+            const int cnt = min(gcnt[cell], kBucketCap);
+            for (int i = 0; i < cnt; ++i) take(gbkt[cell * kBucketCap + i]);
+          }
+      if (whole) break;
+      const float lb = fmaxf((float)r - margin, 0.f) * edge;
+      if (best <= lb * lb * (1.0f - 1.0f / 256.0f)) break;
+      if (lb > ub) break;   // every centroid beyond lies farther than the bound
     }
-    // the shell of ring r (cells at Chebyshev distance exactly r)
-    for (int z = lo[2]; z <= hi[2]; ++z)
-      for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) {
-          const int cheb = max(max(abs(x - cc[0]), abs(y - cc[1])), abs(z - cc[2]));
-          if (cheb != r) continue;
-          const long long cell = ((long long)z * G.dims[1] + y) * G.dims[0] + x;
-          const int cnt = min(gcnt[cell], kBucketCap);
-          for (int i = 0; i < cnt; ++i) take(gbkt[cell * kBucketCap + i]);
-        }
-    if (whole) break;
-    const float lb = fmaxf((float)r - margin, 0.f) * edge;
-    if (best <= lb * lb * (1.0f - 1.0f / 256.0f)) break;
+    if (best < INFINITY || !(ub < INFINITY)) break;
+    ub = INFINITY;   // nothing within the bound after rounding: search unbounded
   }
   A.cb2[j] = best * (1.0f - 1.0f / 256.0f);
 }
 
-cudaError_t launch_cbound(const IterArgs& A, int par, int d, cudaStream_t s) {
-  k_cbound<<<ceil_div(A.k, kBlockThreads), kBlockThreads, 0, s>>>(A, par, d);
+cudaError_t launch_cbound(const IterArgs& A, int par, int d, int use_ub, cudaStream_t s) {
+  k_cbound<<<ceil_div(A.k, kBlockThreads), kBlockThreads, 0, s>>>(A, par, d, use_ub);
   return cudaGetLastError();
 }
 

@@ -151,9 +151,19 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
         iz = A.iz[i];
       }
     } else {
-      for (int j = 0; j < k; ++j) m = fminf(m, sqd<D>(p, sc[j], dv));
+      // one sweep (online softmax normaliser, Milakov & Gimelshein 2018):
+      // z = sum_j exp((m - D_ij) / tau) for the running minimum m, rescaled
+      // by exp((m_new - m_old) / tau) <= 1 whenever the minimum drops
       float z = 0.f;
-      for (int j = 0; j < k; ++j) z += __expf((m - sqd<D>(p, sc[j], dv)) * it);
+      for (int j = 0; j < k; ++j) {
+        const float sj = sqd<D>(p, sc[j], dv);
+        if (sj < m) {
+          z = __fmaf_rn(z, __expf((sj - m) * it), 1.f);
+          m = sj;
+        } else {
+          z += __expf((m - sj) * it);
+        }
+      }
       iz = 1.f / z;
     }
     if (MODE == kRowLoss || MODE == kRowLossBwd) {

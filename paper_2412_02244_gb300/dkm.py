@@ -55,7 +55,8 @@ class dkm_stats(ctypes.Structure):
     _fields_ = [("evals_per_point", ctypes.c_double), ("candidates_per_tile", ctypes.c_double),
                 ("fallback_tiles", ctypes.c_int64), ("stayed_tiles", ctypes.c_int64),
                 ("grid_overflow", ctypes.c_int64),
-                ("tiles", ctypes.c_int64), ("tile_level", ctypes.c_int), ("passes", ctypes.c_int)]
+                ("tiles", ctypes.c_int64), ("tile_level", ctypes.c_int), ("passes", ctypes.c_int),
+                ("stayed_points", ctypes.c_int64)]
 
 
 class dkm_tuning(ctypes.Structure):

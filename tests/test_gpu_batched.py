@@ -205,7 +205,8 @@ def test_batched_uneven_workload_full_size(dkm, oracle):
                                      dict(sort_max=32), dict(sort_max=16),
                                      dict(tile_group=4), dict(tile_group=32),
                                      dict(tile_group=8, sort_max=32), dict(stay_test=1),
-                                     dict(stay_test=1, sort_max=32)])
+                                     dict(stay_test=1, sort_max=32), dict(stay_test=2),
+                                     dict(stay_test=2, row_filter_min=16)])
 def test_tuning_settings_keep_labels_exact(dkm, oracle, setting):
     """Every index setting labels exactly like brute force, and cloud by
     cloud like the FP64 oracle (near-ties aside); the setting's own update
@@ -225,12 +226,15 @@ def test_tuning_settings_keep_labels_exact(dkm, oracle, setting):
     C = init.copy()
     flips = 0
     stays = 0
+    pstays = 0
     for _ in range(6):
         lab, sse, _ = gpu_assign(dkm, ctx, C)
         lab_b, sse_b, _ = gpu_assign(dkm, ctx_b, C)
         assert np.array_equal(lab, lab_b)
         assert abs(sse - sse_b) <= 1e-6 * sse_b
-        stays += dkm.dkm_last_stats(ctx).stayed_tiles
+        st = dkm.dkm_last_stats(ctx)
+        stays += st.stayed_tiles
+        pstays += st.stayed_points
         C_g, _ = gpu_update(dkm, ctx, None, C)
         C_next = np.empty_like(C)
         for b in range(len(ks)):
@@ -246,6 +250,8 @@ def test_tuning_settings_keep_labels_exact(dkm, oracle, setting):
     assert flips <= 2
     if setting.get("stay_test"):
         assert stays > 0
+    if setting.get("stay_test") == 2:
+        assert pstays > 0
 
 
 def test_autotune_choice_cache_and_exactness(dkm):
@@ -258,7 +264,7 @@ def test_autotune_choice_cache_and_exactness(dkm):
     assert t.cells_per_centroid in (0.5, 1.0, 2.0, 4.0)
     assert t.tile_cut_div in (1, 2, 4, 8, 16, 32) and t.row_filter_min in (16, 32, 48, 96, 256)
     assert t.sort_max in (0, 16, 32) and t.tile_group in (1, 2, 4, 8, 16)
-    assert t.stay_test in (0, 1)
+    assert t.stay_test in (0, 1, 2)
     cur = dkm.dkm_get_tuning(ctx)
     assert (cur.cells_per_centroid, cur.tile_cut_div, cur.row_filter_min) == \
         (t.cells_per_centroid, t.tile_cut_div, t.row_filter_min)
@@ -276,7 +282,7 @@ def test_tuning_rejects_bad_values(dkm):
     ctx = _ctx(dkm, P, off, ks)
     for kw in (dict(cells_per_centroid=0.0), dict(cells_per_centroid=100.0),
                dict(tile_cut_div=0), dict(row_filter_min=-1), dict(sort_max=33),
-               dict(tile_group=0), dict(tile_group=33), dict(stay_test=2)):
+               dict(tile_group=0), dict(tile_group=33), dict(stay_test=3)):
         with pytest.raises(dkm.DkmError) as e:
             dkm.dkm_set_tuning(ctx, **kw)
         assert e.value.status == dkm.DKM_EINVAL
@@ -284,8 +290,9 @@ def test_tuning_rejects_bad_values(dkm):
         dkm.dkm_autotune(ctx, dev(init), passes=0)
 
 
+@pytest.mark.parametrize("level", [1, 2])
 @pytest.mark.parametrize("batched", [False, True])
-def test_stay_test_gives_the_same_run_bit_for_bit(dkm, oracle, batched):
+def test_stay_test_gives_the_same_run_bit_for_bit(dkm, oracle, batched, level):
     """The bound layer only skips searches whose outcome it has proved, so a
     run with it equals the run without it in every bit, and near
     convergence some tiles do stay."""
@@ -296,7 +303,7 @@ def test_stay_test_gives_the_same_run_bit_for_bit(dkm, oracle, batched):
         P, init = np.ascontiguousarray(w.points), w.init
         off, ks = np.array([0, w.n], np.int64), np.array([w.k], np.int32)
     out = []
-    for stay in (0, 1):
+    for stay in (0, level):
         ctx = _ctx(dkm, P, off, ks, early_stop=0)
         dkm.dkm_set_tuning(ctx, stay_test=stay)
         out.append(_run(dkm, ctx, init, 12))
@@ -305,6 +312,8 @@ def test_stay_test_gives_the_same_run_bit_for_bit(dkm, oracle, batched):
             assert st.stayed_tiles > 0
         else:
             assert st.stayed_tiles == 0
+        if stay == 2:
+            assert st.stayed_points > 0
     (C0, l0, i0, s0), (C1, l1, i1, s1) = out
     assert np.array_equal(C0, C1) and np.array_equal(l0, l1)
     assert np.array_equal(i0, i1) and np.array_equal(s0, s1)
@@ -312,7 +321,7 @@ def test_stay_test_gives_the_same_run_bit_for_bit(dkm, oracle, batched):
     # pass with the stay test from the run's final centroids labels every
     # cloud like the oracle (near-ties aside) and updates like the oracle
     ctx = _ctx(dkm, P, off, ks, early_stop=0)
-    dkm.dkm_set_tuning(ctx, stay_test=1)
+    dkm.dkm_set_tuning(ctx, stay_test=level)
     _run(dkm, ctx, init, 12)
     lab, _, _ = gpu_assign(dkm, ctx, C1)
     C_g, _ = gpu_update(dkm, ctx, None, C1)

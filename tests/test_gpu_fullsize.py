@@ -21,8 +21,9 @@ every context receives the same FP32 centroids C_t.
     labels).
   - Then C_{t+1} = the oracle's update, rounded to FP32.
 The index settings are the defaults, the autotuner's usual choice on these
-workloads (tile_cut_div 2, row filter off), the bound layer (stay test)
-and hierarchical tiles (tile_group 4).  The free-running runs of the two 2D
+workloads (tile_cut_div 2, row filter off), the bound layer (the tile stay
+test, and the tile and point stay tests) and hierarchical tiles
+(tile_group 4).  The free-running runs of the two 2D
 workloads are replayed pass by pass and compared with oracle.fit."""
 import numpy as np
 import pytest
@@ -38,6 +39,7 @@ SETTINGS = {
     "default": {},
     "tuned": dict(tile_cut_div=2, row_filter_min=256),
     "stay": dict(tile_cut_div=2, row_filter_min=256, stay_test=1),
+    "pstay": dict(tile_cut_div=2, row_filter_min=256, stay_test=2),
     "group4": dict(tile_group=4),
 }
 
@@ -67,6 +69,7 @@ def _lockstep(dkm, oracle, w, passes, sample=None, seed=0, stop_when_stable=Fals
     C = w.init.copy()
     flips = 0
     stays = 0
+    pstays = 0
     prev_o = None
     for t in range(passes):
         C64 = C.astype(np.float64)
@@ -93,12 +96,15 @@ def _lockstep(dkm, oracle, w, passes, sample=None, seed=0, stop_when_stable=Fals
                 f"pass {t}, {name}: centroid error {err:.3g} > {CENTROID_TOL * ext:.3g}"
             if name == "stay":
                 stays = max(stays, dkm.dkm_last_stats(ctx).stayed_tiles)
+            if name == "pstay":
+                pstays = max(pstays, dkm.dkm_last_stats(ctx).stayed_points)
         C = C_o.astype(np.float32)
         if stop_when_stable and prev_o is not None and np.array_equal(lab_o, prev_o):
             break
         prev_o = lab_o
     for ctx in list(ctxs.values()) + [ctx_b]:
         ctx.close()
+    assert pstays > 0
     return flips, stays
 
 
