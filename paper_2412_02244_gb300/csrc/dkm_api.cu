@@ -169,7 +169,7 @@ struct Layout {
 struct ArenaPlan {
   size_t xs, ys, zs, keys0, keys1, vals0, vals1, rs_scratch, tbox, tiles,
       tcloud, tfirst, kcloud, ubox, ucloud, ufirst, tunit, cb2, drift, tlab, tl_scratch, level_hist, doff, dcoff, clouds, crun, cacc, lab, cw, acc, slots,
-      st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, cstage, cstage2,
+      st, gcnt0, gcnt1, gbkt0, gbkt1, ovf0, ovf1, ovf_cnt0, ovf_cnt1, tlist, tcnt, tref, cstage, cstage2,
       kstage, total;
 };
 
@@ -229,6 +229,7 @@ ArenaPlan arena_plan(int64_t n, int d, int64_t k, int64_t B, int64_t max_cells, 
   P.ovf_cnt1 = L.take<int>(B);
   P.tlist = L.take<float4>(tm * kTileCap);
   P.tcnt = L.take<int>(tm);
+  P.tref = L.take<int>(tm);
   P.cstage = L.take<float>((size_t)k * d);
   P.cstage2 = L.take<float>((size_t)k * d);
   P.kstage = L.take<int32_t>(k);
@@ -283,6 +284,7 @@ IterArgs iter_args(const dkm_ctx* c, int track_changes, int early_stop) {
   }
   A.tlist = c->tlist;
   A.tcnt = c->tcnt;
+  A.tref = c->tref;
   A.sse_hist = c->sse_hist;
   A.chg_hist = c->chg_hist;
   A.track_changes = track_changes;
@@ -678,7 +680,10 @@ dkm_status apply_tiling(dkm_ctx* c) {
 // (dkm_setup) and are cleared when the tiles or units are re-cut
 // (reset_lists).  The stay test's single labels always are.
 dkm_status apply_units(dkm_ctx* c, bool reset_lists) {
-  if (reset_lists) DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
+  if (reset_lists) {
+    DKM_CK(cudaMemsetAsync(c->tcnt, 0, sizeof(int) * c->tiles_cap, c->stream));
+    DKM_CK(cudaMemsetAsync(c->tref, 0xff, sizeof(int) * c->tiles_cap, c->stream));
+  }
   DKM_CK(cudaMemsetAsync(c->tlab, 0xff, sizeof(int) * c->tiles_cap, c->stream));
   if (c->unit_g <= 1) {
     c->n_units = c->n_tiles;
@@ -888,6 +893,7 @@ dkm_status create_impl(dkm_ctx** out, const float* points, const std::vector<int
   c->ovf_cnt[1] = (int*)(base + P.ovf_cnt1);
   c->tlist = (float4*)(base + P.tlist);
   c->tcnt = (int*)(base + P.tcnt);
+  c->tref = (int*)(base + P.tref);
   c->cstage = (float*)(base + P.cstage);
   c->cstage2 = (float*)(base + P.cstage2);
   c->kstage = (int32_t*)(base + P.kstage);

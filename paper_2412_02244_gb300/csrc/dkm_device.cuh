@@ -155,6 +155,7 @@ struct IterArgs {
   int* ovf_cnt[2];           // per cloud overflow count, two parities
   float4* tlist;             // per unit kTileCap candidates (x, y, z, id bits; unordered)
   int* tcnt;                 // per unit list length (> kTileCap = overflow)
+  int* tref;                 // per unit: id of the last search's bound-defining centroid (-1: none)
   double* sse_hist;
   unsigned long long* chg_hist;
   int track_changes;         // read previous labels and count changes

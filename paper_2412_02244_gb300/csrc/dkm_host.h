@@ -135,6 +135,7 @@ struct dkm_ctx {
   int* ovf_cnt[2] = {nullptr, nullptr};
   float4* tlist = nullptr;     // per tile kTileCap candidates of the last search
   int* tcnt = nullptr;
+  int* tref = nullptr;         // per unit: the last search's bound-defining centroid
   float* cstage = nullptr;     // k x d centroid staging
   float* cstage2 = nullptr;    // k x d centroid output staging
   int32_t* kstage = nullptr;   // k counts staging

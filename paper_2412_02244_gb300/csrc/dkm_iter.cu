@@ -285,6 +285,17 @@ __device__ __forceinline__ void clear_other_parity(const IterArgs& A, int par) {
   for (long long c = g; c < A.B; c += stride) A.ovf_cnt[par ^ 1][c] = 0;
 }
 
+// Keep the candidate with the smallest maxd^2 over the box seen so far (the
+// best bound of the next pass's phase A).
+__device__ __forceinline__ void note_ref(const float4& lo, const float4& hi, const float4& c,
+                                         int d, float& ref_m, int& ref_id) {
+  const float mc = maxd2(lo, hi, c.x, c.y, c.z, d);
+  if (mc < ref_m) {
+    ref_m = mc;
+    ref_id = __float_as_int(c.w);
+  }
+}
+
 // The candidate search of search unit t (one warp), list to tlist / tcnt.
 // MULTI = false: a single cloud, whose table entry is read from the kernel
 // parameters (constant bank) instead of global memory.
@@ -306,6 +317,7 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
         if (lane == 0) {
           out[0] = c;
           A.tcnt[t] = 1;
+          A.tref[t] = a;
           if (A.want_stats) {
             Slot& s = A.slots[t & (kSlots - 1)];
             red_add_u64(&s.cands, 1ull);
@@ -334,25 +346,24 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
 
   // ---- phase A ----
   // Any centroid of the cloud bounds the nearest distance of every point in
-  // the box by maxd(box, c).  The tile's list of the previous pass holds
-  // ids near the tile, so its current positions give U in one load round;
-  // ids outside the cloud (a list left by another tiling) are skipped.
-  // Without a usable list, rings of cells around the box are scanned.
-  // The centroid that gives U (r1) also serves as the dominance reference
-  // of phase B.
+  // the box by maxd(box, c).  The candidate of the previous pass's list with
+  // the smallest maxd over the box (tref) lies near the tile, so its
+  // current position gives U in one load; an id outside the cloud (left by
+  // another tiling) is not used.  Without a usable reference, rings of cells around the box
+  // are scanned.  The centroid that gives U (r1) also serves as the
+  // dominance reference of phase B (the kNN bound inherited from the
+  // previous pass, in the spirit of Section IV-A's bounds from parent
+  // nodes).
   float u2 = INFINITY;
   float m = INFINITY;
   float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f);   // this lane's best so far
-  const int q_old = A.tcnt[t];
-  if (q_old >= 1 && q_old <= kTileCap) {
-    for (int j = lane; j < q_old; j += 32) {
-      const int id = __float_as_int(out[j].w);
-      if (id < c0 || id >= c1) continue;
-      const float4 c = A.cw[id];
-      const float mc = maxd2(lo, hi, c.x, c.y, c.z, d);
-      if (mc < m) { m = mc; r1 = c; }
-    }
-    u2 = warp_min_nonneg(m);   // every lane has read its old ids before any is overwritten
+  const int ref = A.tref[t];
+  if (ref >= c0 && ref < c1) {
+    // the previous pass's reference centroid, at its current position: one
+    // dependent load, the same on every lane
+    r1 = A.cw[ref];
+    m = maxd2(lo, hi, r1.x, r1.y, r1.z, d);
+    u2 = m;
   }
   for (int ring = 0; !(u2 < INFINITY); ring = ring ? 2 * ring : 1) {
     int rlo[3], rhi[3];
@@ -407,7 +418,9 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
     r1.x = __shfl_sync(0xffffffffu, r1.x, src);
     r1.y = __shfl_sync(0xffffffffu, r1.y, src);
     r1.z = __shfl_sync(0xffffffffu, r1.z, src);
+    r1.w = __shfl_sync(0xffffffffu, r1.w, src);
   }
+
 
   // ---- phase B ----
   // keep: within the ball bound (mind^2 <= U^2 kKeep) and not dominated
@@ -428,6 +441,8 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   const long long ncell = (long long)nx * ny * (rhi[2] - rlo[2] + 1);
   const unsigned lt = (1u << lane) - 1u;
   int count = 0;
+  float ref_m = INFINITY;   // the kept candidate with the smallest maxd^2: the next reference
+  int ref_id = -1;
   if (ncell > flat_cells) {
     // every centroid of the cloud once; the overflow list is then redundant
     for (int j0 = c0; j0 < c1; j0 += 32) {
@@ -439,6 +454,7 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
         keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k &&
                !dominated(lo, hi, r1, slack, c.x, c.y, c.z, d);
       }
+      if (keep) note_ref(lo, hi, c, d, ref_m, ref_id);
       unsigned bal = __ballot_sync(0xffffffffu, keep);
       int pos = count + __popc(bal & lt);
       if (keep && pos < kTileCap) out[pos] = c;
@@ -487,6 +503,7 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
           e = gbkt[cl * kBucketCap + slot];
           keep = mind2(lo, hi, e.x, e.y, e.z, d) <= u2k &&
                  !dominated(lo, hi, r1, slack, e.x, e.y, e.z, d);
+          if (keep) note_ref(lo, hi, e, d, ref_m, ref_id);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = count + __popc(bal & lt);
@@ -504,6 +521,7 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
           c = ovf[q];
           keep = mind2(lo, hi, c.x, c.y, c.z, d) <= u2k &&
                  !dominated(lo, hi, r1, slack, c.x, c.y, c.z, d);
+          if (keep) note_ref(lo, hi, c, d, ref_m, ref_id);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         int pos = count + __popc(bal & lt);
@@ -511,6 +529,12 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
         count += __popc(bal);
       }
     }
+  }
+  {
+    const float bm = warp_min_nonneg(ref_m);
+    const int src = __ffs(__ballot_sync(0xffffffffu, ref_m == bm)) - 1;
+    const int rid = __shfl_sync(0xffffffffu, ref_id, src);
+    if (lane == 0) A.tref[t] = rid;
   }
   if (lane == 0) {
     A.tcnt[t] = count;
@@ -525,7 +549,8 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
 template <bool MULTI>
 __global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
     k_search(const __grid_constant__ IterArgs A, int par, int d) {
-  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
+  // every cloud stopped (fixed during this kernel; only early-stopping runs stop)
+  if (A.early_stop && A.st->n_done == A.B) return;
   clear_other_parity(A, par);
   const int t = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
   if (t >= A.n_units) return;   // t: the search unit (a tile or a group of tiles)
@@ -1348,7 +1373,8 @@ __global__ void __launch_bounds__(32 * kAssignWarps, DKM_ASSIGN_MIN_WARPS / kAss
   __shared__ unsigned short s_r[kAssignWarps][kTileCap];
   __shared__ float slb[kAssignWarps][32];
   __shared__ int4 s_acc[kAssignWarps][32];
-  if (A.st->n_done == A.B) return;   // every cloud stopped (fixed during this kernel)
+  // every cloud stopped (fixed during this kernel; only early-stopping runs stop)
+  if (A.early_stop && A.st->n_done == A.B) return;
   const int w = threadIdx.x >> 5;
   const int t = blockIdx.x * kAssignWarps + w;
   if (t >= A.n_tiles) return;   // warp-level exits, no CTA barrier below
