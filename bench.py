@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "6646a5afc6f4a134", "bytes_per_launch": 129_772_800 + 23_162_880,
+NCU_TRAFFIC = {"sha": "a0dec2d771db8947", "bytes_per_launch": 129_608_704 + 22_585_344,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
@@ -326,7 +326,8 @@ def launches_per_step(iters: int) -> int:
 DEFAULT_TUNING = dict(cells_per_centroid=1.0, tile_cut_div=8, row_filter_min=48, sort_max=0,
                       tile_group=1, stay_test=0)
 ABLATIONS = [
-    ("stay_test (bound layer)", {"stay_test": 1}),
+    ("stay_test 1 (bound layer: tile test)", {"stay_test": 1}),
+    ("stay_test 2 (bound layer: tile and point tests)", {"stay_test": 2}),
     ("tile_group 4 (hierarchical tiles)", {"tile_group": 4}),
     ("tile_group 8 (hierarchical tiles)", {"tile_group": 8}),
     ("sort_max 32 (sorted early exit)", {"sort_max": 32}),
@@ -360,9 +361,11 @@ def bench_ablations(dkm, pts, n, d, k, C, stream, tune):
             ms.append(T.search_ms + T.assign_ms + T.update_ms)
         st = dkm.dkm_last_stats(ctx)
         out.append({"setting": name, "ms_per_pass": float(np.median(ms[1:])),
+                    "search_ms": T.search_ms, "assign_ms": T.assign_ms, "update_ms": T.update_ms,
                     "evals_per_point": st.evals_per_point,
                     "candidates_per_tile": st.candidates_per_tile, "tiles": st.tiles,
-                    "stayed_tiles": st.stayed_tiles})
+                    "stayed_tiles": st.stayed_tiles, "stayed_points": st.stayed_points,
+                    "stayed_point_fraction": st.stayed_points / n})
     ctx.close()
     return {"from": "one pass from the timed run's final centroids per setting",
             "settings": out}
@@ -415,6 +418,19 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
     Ti = dkm.dkm_last_timings(ctx)
     per_b = Tb.search_ms + Tb.assign_ms + Tb.update_ms
     per_i = Ti.search_ms + Ti.assign_ms + Ti.update_ms
+    # the bound layer's stay tests from the run's final centroids (two
+    # passes, the second measured): how many tiles and points keep their label
+    stays = []
+    for level in (1, 2):
+        t = dkm.dkm_get_tuning(ctx)
+        dkm.dkm_set_tuning(ctx, tile_group=1, stay_test=level)
+        dkm.dkm_run_batched(ctx, C, 2, Cb, lb)
+        ss = dkm.dkm_last_stats(ctx)
+        stays.append({"stay_test": level, "pass": 2,
+                      "stayed_tiles": ss.stayed_tiles, "tiles": ss.tiles,
+                      "stayed_points": ss.stayed_points, "stayed_point_fraction": ss.stayed_points / n,
+                      "evals_per_point": ss.evals_per_point})
+        dkm.dkm_set_tuning(ctx, t)
     cb.close()
     ctx.close()
     am = float(np.mean(a_ms))
@@ -437,6 +453,7 @@ def bench_batched(dkm, torch, dev, stream, steps: int, hbm: float):
             "brute_force": {"ms_per_pass": per_b, "indexed_ms_per_pass": per_i,
                             "speedup_indexed_over_brute": per_b / per_i if per_i > 0 else None,
                             "from": "final centroids of the timed run, 2 passes each"},
+            "bound_layer": stays,
             "launches_per_pass": 3}
 
 
@@ -811,6 +828,7 @@ def run_ours(args):
                        "candidates_per_tile": stats.candidates_per_tile,
                        "fallback_tiles": stats.fallback_tiles,
                        "stayed_tiles": stats.stayed_tiles,
+                       "stayed_points": stats.stayed_points,
                        "tiles": stats.tiles, "tile_level": stats.tile_level,
                        "grid_overflow": stats.grid_overflow}
     line["steady_state"] = ("every timed step repeats dkm_setup + dkm_run on the same context: "
