@@ -336,14 +336,6 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   // of the cloud once, so large ranges scan the flat centroid array instead
   const long long flat_cells = (long long)(cl.k / 4) + 32;
 
-  int clo[3], chi[3];
-  clo[0] = cell_coord(lo.x, G.g0[0], G.inv_s, G.dims[0]);
-  chi[0] = cell_coord(hi.x, G.g0[0], G.inv_s, G.dims[0]);
-  clo[1] = cell_coord(lo.y, G.g0[1], G.inv_s, G.dims[1]);
-  chi[1] = cell_coord(hi.y, G.g0[1], G.inv_s, G.dims[1]);
-  clo[2] = d == 3 ? cell_coord(lo.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
-  chi[2] = d == 3 ? cell_coord(hi.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
-
   // ---- phase A ----
   // Any centroid of the cloud bounds the nearest distance of every point in
   // the box by maxd(box, c).  The candidate of the previous pass's list with
@@ -364,6 +356,15 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
     r1 = A.cw[ref];
     m = maxd2(lo, hi, r1.x, r1.y, r1.z, d);
     u2 = m;
+  }
+  int clo[3], chi[3];   // the box's own cells (only the ring search needs them)
+  if (!(u2 < INFINITY)) {
+    clo[0] = cell_coord(lo.x, G.g0[0], G.inv_s, G.dims[0]);
+    chi[0] = cell_coord(hi.x, G.g0[0], G.inv_s, G.dims[0]);
+    clo[1] = cell_coord(lo.y, G.g0[1], G.inv_s, G.dims[1]);
+    chi[1] = cell_coord(hi.y, G.g0[1], G.inv_s, G.dims[1]);
+    clo[2] = d == 3 ? cell_coord(lo.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
+    chi[2] = d == 3 ? cell_coord(hi.z, G.g0[2], G.inv_s, G.dims[2]) : 0;
   }
   for (int ring = 0; !(u2 < INFINITY); ring = ring ? 2 * ring : 1) {
     int rlo[3], rhi[3];
@@ -1059,14 +1060,19 @@ __device__ __forceinline__ void load_points(const IterArgs& A, int D, int64_t ba
                                             float2 (&y)[kRowsPerWarp], float2 (&z)[kRowsPerWarp],
                                             bool (&va)[kRowsPerWarp], bool (&vb)[kRowsPerWarp]) {
   const int lane = threadIdx.x & 31;
+  // window-relative 32-bit offsets: one 64-bit address per coordinate row
+  const float* __restrict__ px = A.xs + base;
+  const float* __restrict__ py = A.ys + base;
+  const float* __restrict__ pz = A.zs + base;
+  const int lo = (int)(vlo - base), hi = (int)(vhi - base);
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
-    int64_t i = base + r * kRowPts + 2 * lane;
-    x[r] = *reinterpret_cast<const float2*>(A.xs + i);
-    y[r] = *reinterpret_cast<const float2*>(A.ys + i);
-    z[r] = D == 3 ? *reinterpret_cast<const float2*>(A.zs + i) : make_float2(0.f, 0.f);
-    va[r] = i >= vlo && i < vhi;
-    vb[r] = i + 1 >= vlo && i + 1 < vhi;
+    const int o = r * kRowPts + 2 * lane;
+    x[r] = *reinterpret_cast<const float2*>(px + o);
+    y[r] = *reinterpret_cast<const float2*>(py + o);
+    z[r] = D == 3 ? *reinterpret_cast<const float2*>(pz + o) : make_float2(0.f, 0.f);
+    va[r] = o >= lo && o < hi;
+    vb[r] = o + 1 >= lo && o + 1 < hi;
   }
 }
 
@@ -1089,10 +1095,15 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
   Pts<D> P;
   bool va[kRowsPerWarp], vb[kRowsPerWarp];
   load_points(A, D, base, se.x, se.y, P.x, P.y, P.z, va, vb);
+  // valid points per row: the tile's range [lo, hi) of the window cut by
+  // the row's [64 r, 64 r + 64) (warp-uniform arithmetic)
   int nv_row[kRowsPerWarp];
+  {
+    const int lo = se.x - (int)base, hi = se.y - (int)base;
 #pragma unroll
-  for (int r = 0; r < kRowsPerWarp; ++r)
-    nv_row[r] = __popc(__ballot_sync(0xffffffffu, va[r])) + __popc(__ballot_sync(0xffffffffu, vb[r]));
+    for (int r = 0; r < kRowsPerWarp; ++r)
+      nv_row[r] = max(0, min(hi, (r + 1) * kRowPts) - max(lo, r * kRowPts));
+  }
   const int nv_tile = se.y - se.x;
 
   float2 best[kRowsPerWarp];
@@ -1311,21 +1322,22 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
     m2 = fmaxf(m2, fmaxf(va[r] ? best[r].x : 0.f, vb[r] ? best[r].y : 0.f));
   }
   if (PSTAY && any_pstay) slots = false;   // the kept labels carry no list position
+  int32_t* __restrict__ wlab = A.lab + base;   // the window's labels (32-bit offsets)
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
     if (nv_row[r] == 0) continue;   // warp-uniform
-    const int64_t i = base + r * kRowPts + 2 * lane;
+    const int o = r * kRowPts + 2 * lane;
     const int la = lb[2 * r], lc = lb[2 * r + 1];
     if (A.track_changes) {
-      int pa = va[r] ? A.lab[i] : la, pb = vb[r] ? A.lab[i + 1] : lc;
+      int pa = va[r] ? wlab[o] : la, pb = vb[r] ? wlab[o + 1] : lc;
       changed += (int)(pa != la) + (int)(pb != lc);
     }
     if (va[r] && vb[r]) {
-      *reinterpret_cast<int2*>(A.lab + i) = make_int2(la, lc);
+      *reinterpret_cast<int2*>(wlab + o) = make_int2(la, lc);
     } else if (va[r]) {
-      A.lab[i] = la;
+      wlab[o] = la;
     } else if (vb[r]) {
-      A.lab[i + 1] = lc;
+      wlab[o + 1] = lc;
     }
   }
   if (A.want_sse) sse = tile_sse(best, va, vb, s_sse);
