@@ -299,8 +299,9 @@ __device__ __forceinline__ void note_ref(const float4& lo, const float4& hi, con
 // The candidate search of search unit t (one warp), list to tlist / tcnt.
 // MULTI = false: a single cloud, whose table entry is read from the kernel
 // parameters (constant bank) instead of global memory.
-template <bool MULTI>
-__device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, int t) {
+template <bool MULTI, int D>
+__device__ __forceinline__ void search_unit(const IterArgs& A, int par, int t) {
+  constexpr int d = D;
   const int lane = threadIdx.x & 31;
   const int b = MULTI ? A.ucloud[t] : 0;
   if (MULTI && A.crun[b].done) return;
@@ -470,12 +471,12 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
     bool any_ovf = false;   // a cell of the range overflowed into the list
     for (long long q0 = 0; q0 < ncell; q0 += 32) {
       const long long q = q0 + lane;
-      long long cell = 0;
+      int cell = 0;   // within the cloud's grid (fewer than 2^31 cells: they fit device memory)
       int cnt = 0;
       if (q < ncell) {
         int ox, oy, oz;
         decode_cell(q, nx, ny, ox, oy, oz);
-        cell = cell_index(G, rlo[0] + ox, rlo[1] + oy, rlo[2] + oz);
+        cell = ((rlo[2] + oz) * G.dims[1] + (rlo[1] + oy)) * G.dims[0] + (rlo[0] + ox);
         const int raw = gcnt[cell];
         any_ovf = any_ovf || raw > kBucketCap;
         cnt = min(raw, kBucketCap);
@@ -496,7 +497,7 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
           const int e = __shfl_sync(0xffffffffu, excl, L + step);
           if (e <= j) L += step;
         }
-        const long long cl = __shfl_sync(0xffffffffu, cell, L);
+        const int cl = __shfl_sync(0xffffffffu, cell, L);
         const int slot = j - __shfl_sync(0xffffffffu, excl, L);
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
         bool keep = false;
@@ -547,15 +548,15 @@ __device__ __forceinline__ void search_unit(const IterArgs& A, int par, int d, i
   }
 }
 
-template <bool MULTI>
+template <bool MULTI, int D>
 __global__ void __launch_bounds__(32 * kSearchWarps, DKM_SEARCH_MIN_BLOCKS)
-    k_search(const __grid_constant__ IterArgs A, int par, int d) {
+    k_search(const __grid_constant__ IterArgs A, int par) {
   // every cloud stopped (fixed during this kernel; only early-stopping runs stop)
   if (A.early_stop && A.st->n_done == A.B) return;
   clear_other_parity(A, par);
   const int t = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
   if (t >= A.n_units) return;   // t: the search unit (a tile or a group of tiles)
-  search_unit<MULTI>(A, par, d, t);
+  search_unit<MULTI, D>(A, par, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1508,8 +1509,13 @@ cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const fl
 
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
   const int g = ceil_div(A.n_units, kSearchWarps);
-  if (A.B > 1) k_search<true><<<g, 32 * kSearchWarps, 0, s>>>(A, par, d);
-  else k_search<false><<<g, 32 * kSearchWarps, 0, s>>>(A, par, d);
+  if (d == 3) {
+    if (A.B > 1) k_search<true, 3><<<g, 32 * kSearchWarps, 0, s>>>(A, par);
+    else k_search<false, 3><<<g, 32 * kSearchWarps, 0, s>>>(A, par);
+  } else {
+    if (A.B > 1) k_search<true, 2><<<g, 32 * kSearchWarps, 0, s>>>(A, par);
+    else k_search<false, 2><<<g, 32 * kSearchWarps, 0, s>>>(A, par);
+  }
   return cudaGetLastError();
 }
 
