@@ -252,6 +252,18 @@ __device__ __forceinline__ void fixed_exponents_box(const unsigned* pbox, const 
   *s_sse = 60 - en - 2 * eE;
 }
 
+// One coordinate of the refine step's new centroid, c + s 2^-s_glob / cnt
+// (s: the fixed-point residual sum of the cluster, cnt > 0: its size), in
+// FP32: the sum and the count converted once (relative error 2^-24 each),
+// one correctly rounded division, an exact power-of-two scaling and the
+// final addition.  The result lies within a few ulp of the exactly rounded
+// mean, and no FP64 arithmetic is needed (its rate on this GPU is a small
+// fraction of FP32's).
+__device__ __forceinline__ float refine_coord(float c, long long s, long long cnt, int s_glob) {
+  const float m = __fdiv_rn(__ll2float_rn(s), __ll2float_rn(cnt));
+  return __fadd_rn(c, ldexpf(m, -s_glob));
+}
+
 __device__ __forceinline__ void fixed_exponents(const DevState* st, int64_t n, int* s_glob,
                                                 int* s_sse) {
   fixed_exponents_box(st->pbox, st->cbox, n, s_glob, s_sse);

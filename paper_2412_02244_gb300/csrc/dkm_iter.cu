@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
     collect_pass(A, t);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= A.k) return;
-  const int b = A.kcloud[j];
-  if (mode == 1 && t >= 0 && A.crun[b].passes != t + 1) return;   // stopped earlier
+  const int b = A.B > 1 ? A.kcloud[j] : 0;
+  // a cloud that stopped earlier (only early-stopping runs stop clouds)
+  if (mode == 1 && t >= 0 && A.early_stop && A.crun[b].passes != t + 1) return;
   float4 c;
   if (mode == 0) {
     c.x = user_c[(int64_t)j * d + 0];
@@ -183,10 +184,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
     if (counts_out) counts_out[j] = (int32_t)cnt;
     const float4 c_old = c;
     if (cnt > 0) {
-      const double u = exp2(-(double)A.crun[b].s_glob) / (double)cnt;
-      c.x = (float)((double)c.x + (double)(long long)a.s[0] * u);
-      c.y = (float)((double)c.y + (double)(long long)a.s[1] * u);
-      if (d == 3) c.z = (float)((double)c.z + (double)(long long)a.s[2] * u);
+      const int s_glob = A.crun[b].s_glob;
+      c.x = refine_coord(c.x, (long long)a.s[0], cnt, s_glob);
+      c.y = refine_coord(c.y, (long long)a.s[1], cnt, s_glob);
+      if (d == 3) c.z = refine_coord(c.z, (long long)a.s[2], cnt, s_glob);
     }
     if (A.stay && t >= 0) {
       // the drift Delta[j] of Algorithm 1's refine step (rounded up) and

@@ -197,10 +197,9 @@ __global__ void k_na_update(const float* __restrict__ C, int k, int d, int64_t n
   const long long cnt = (long long)a.cnt;
   int s_glob, s_sse;
   fixed_exponents(&s->st, n, &s_glob, &s_sse);
-  const double u = cnt > 0 ? exp2(-(double)s_glob) / (double)cnt : 0.0;
   for (int t = 0; t < d; ++t) {
     const float c = C[(int64_t)j * d + t];
-    out[(int64_t)j * d + t] = cnt > 0 ? (float)((double)c + (double)(long long)a.s[t] * u) : c;
+    out[(int64_t)j * d + t] = cnt > 0 ? refine_coord(c, (long long)a.s[t], cnt, s_glob) : c;
   }
 }
 
