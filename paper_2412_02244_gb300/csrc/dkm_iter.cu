@@ -592,12 +592,23 @@ __device__ __forceinline__ void take_min(float s, int id, float& best, int& bid)
   }
 }
 
+// The same choice when the candidates arrive in ascending id order: a
+// strictly smaller distance is then the only way to win (an equal distance
+// came with a lower id earlier), one compare instead of the 64-bit key's two.
+__device__ __forceinline__ void take_min_ordered(float s, int id, float& best, int& bid) {
+  if (s < best) {
+    best = s;
+    bid = id;
+  }
+}
+
 #ifndef DKM_EVAL_UNROLL
 #define DKM_EVAL_UNROLL 1
 #endif
 constexpr int kEvalUnroll = DKM_EVAL_UNROLL;   // candidates per unrolled step
-// all rows of the tile against candidates s_c[idx[j]] (idx == nullptr: s_c[j])
-template <int D>
+// all rows of the tile against candidates s_c[idx[j]] (idx == nullptr:
+// s_c[j]); ORD: the candidates come in ascending id order
+template <int D, bool ORD = false>
 __device__ __forceinline__ void eval_list(const float4* __restrict__ s_c,
                                           const unsigned short* __restrict__ idx, int m,
                                           const Pts<D>& P, float2 (&best)[kRowsPerWarp],
@@ -619,14 +630,19 @@ __device__ __forceinline__ void eval_list(const float4* __restrict__ s_c,
         float2 dz = __fadd2_rn(P.z[r], nz);
         s = __ffma2_rn(dz, dz, s);
       }
-      take_min(s.x, id, best[r].x, bid[r].x);
-      take_min(s.y, id, best[r].y, bid[r].y);
+      if (ORD) {
+        take_min_ordered(s.x, id, best[r].x, bid[r].x);
+        take_min_ordered(s.y, id, best[r].y, bid[r].y);
+      } else {
+        take_min(s.x, id, best[r].x, bid[r].x);
+        take_min(s.y, id, best[r].y, bid[r].y);
+      }
     }
   }
 }
 
 // one row (64 points, two per lane) against candidates s_c[idx[j]]
-template <int D>
+template <int D, bool ORD = false>
 __device__ __forceinline__ void eval_row(const float4* __restrict__ s_c,
                                          const unsigned short* __restrict__ idx, int m, float2 px,
                                          float2 py, float2 pz, float2& best, int2& bid) {
@@ -642,8 +658,13 @@ __device__ __forceinline__ void eval_row(const float4* __restrict__ s_c,
       float2 dz = __fadd2_rn(pz, make_float2(-c.z, -c.z));
       s = __ffma2_rn(dz, dz, s);
     }
-    take_min(s.x, id, best.x, bid.x);
-    take_min(s.y, id, best.y, bid.y);
+    if (ORD) {
+      take_min_ordered(s.x, id, best.x, bid.x);
+      take_min_ordered(s.y, id, best.y, bid.y);
+    } else {
+      take_min(s.x, id, best.x, bid.x);
+      take_min(s.y, id, best.y, bid.y);
+    }
   }
 }
 
@@ -1117,6 +1138,7 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
   }
   unsigned long long evals = 0;   // point x candidate evaluations of this warp
   bool slots = false;             // candidate keys carry list positions (see below)
+  bool ordered = false;           // the staged list is in ascending id order
   int q_tile = 0;                 // length of the staged list
   // point stay test (stay == 2): per point its kept label (or -1) and its
   // squared distance; rows whose valid points all stay
@@ -1131,7 +1153,7 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
       __syncwarp();
       for (int i = lane; i < m; i += 32) sc[i] = A.cw[j0 + i];
       __syncwarp();
-      eval_list<D>(sc, nullptr, m, P, best, bid);
+      eval_list<D, true>(sc, nullptr, m, P, best, bid);   // ids ascend with j
     }
     evals = (unsigned long long)cl.k * nv_tile;
   } else {
@@ -1150,6 +1172,21 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
         // the unit's list holds every candidate of the group's box; narrow
         // it with this tile's own box (the bound of k_search)
         q = filter_list<D>(src, qs, A.tbox[2 * t], A.tbox[2 * t + 1], sc, slots);
+      } else if (qs <= 32) {
+        // a short list is placed in ascending id order (the rank of each
+        // entry among the list's distinct ids), so that the candidate loops
+        // below can keep the lowest id of equal distances by order alone
+        const bool has = lane < qs;
+        float4 c = has ? src[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int id = has ? __float_as_int(c.w) : INT_MAX;
+        int rank = 0;
+        for (int m2 = 0; m2 < qs; ++m2) rank += __shfl_sync(0xffffffffu, id, m2) < id;
+        if (has) {
+          if (slots) c.w = __int_as_float((id << 8) | rank);
+          sc[rank] = c;
+        }
+        __syncwarp();
+        ordered = true;
       } else {
         for (int i = lane; i < qs; i += 32) {
           float4 c = src[i];
@@ -1205,7 +1242,8 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
 #pragma unroll
         for (int r = 0; r < kRowsPerWarp; ++r) {
           if (nv_row[r] == 0 || ((row_stay >> r) & 1u)) continue;   // warp-uniform
-          eval_row<D>(sc, sr, q, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
+          if (ordered) eval_row<D, true>(sc, sr, q, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
+          else eval_row<D>(sc, sr, q, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
           evals += (unsigned long long)q * nv_row[r];
         }
       } else if (q <= A.sort_max) {   // sort_max <= 32
@@ -1248,10 +1286,14 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
           if (nv_row[r] == 0) continue;
           float4 rlo, rhi;
           row_box(P.x[r], P.y[r], P.z[r], va[r], vb[r], rlo, rhi);
-          const int mr = filter_box<D>(sc, q, rlo, rhi, INFINITY, sr);
-          eval_row<D>(sc, sr, mr, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
+          const int mr = filter_box<D>(sc, q, rlo, rhi, INFINITY, sr);   // keeps the order
+          if (ordered) eval_row<D, true>(sc, sr, mr, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
+          else eval_row<D>(sc, sr, mr, P.x[r], P.y[r], P.z[r], best[r], bid[r]);
           evals += (unsigned long long)mr * nv_row[r];
         }
+      } else if (ordered) {
+        eval_list<D, true>(sc, nullptr, q, P, best, bid);
+        evals = (unsigned long long)q * nv_tile;
       } else {
         eval_list<D>(sc, nullptr, q, P, best, bid);
         evals = (unsigned long long)q * nv_tile;
