@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "a0dec2d771db8947", "bytes_per_launch": 129_608_704 + 22_585_344,
+NCU_TRAFFIC = {"sha": "bedabf2e64bea990", "bytes_per_launch": 129_612_800 + 22_892_032,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
