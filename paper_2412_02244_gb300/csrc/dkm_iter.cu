@@ -155,7 +155,7 @@ __global__ void k_reset_run(DevState* st, CloudRun* crun, CloudAcc* cacc, int B)
 //   mode 0: cw[j] = user_c[j]
 //   mode 1: cw[j] += acc mean residual (if the cluster is non-empty); acc cleared
 // With t >= 0 (inside a run) a cloud's centroids are only updated if the
-// cloud executed pass t, and CTA 0 first folds the pass's counters.
+// cloud executed pass t, and an extra CTA folds the pass's counters.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mode, int t, int d,
                                                              const float* __restrict__ user_c,
@@ -163,8 +163,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_centroids(IterArgs A, int mod
                                                              int32_t* __restrict__ counts_out) {
   // (no kernel-wide early exit: n_done changes inside this kernel, so only
   // the per-cloud pass counts, fixed since k_assign, decide what runs)
-  if (mode == 1 && t >= 0 && blockIdx.x == 0 && (A.want_stats || A.early_stop))
+  // The last CTA, beyond the centroids' CTAs, folds the pass's counters, so
+  // that the fold and the updates run side by side (nothing here reads what
+  // the fold writes).
+  const bool fold = mode == 1 && t >= 0 && (A.want_stats || A.early_stop);
+  if (fold && blockIdx.x == gridDim.x - 1) {
     collect_pass(A, t);
+    return;
+  }
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= A.k) return;
   const int b = A.B > 1 ? A.kcloud[j] : 0;
@@ -1545,8 +1551,9 @@ cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s) {
 
 cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const float* user_c,
                              int insert, int par, int32_t* counts_out, cudaStream_t s) {
-  k_centroids<<<ceil_div(A.k, kBlockThreads), kBlockThreads, 0, s>>>(A, mode, t, d, user_c, insert,
-                                                                    par, counts_out);
+  const bool fold = mode == 1 && t >= 0 && (A.want_stats || A.early_stop);   // one more CTA
+  k_centroids<<<ceil_div(A.k, kBlockThreads) + (fold ? 1 : 0), kBlockThreads, 0, s>>>(
+      A, mode, t, d, user_c, insert, par, counts_out);
   return cudaGetLastError();
 }
 
