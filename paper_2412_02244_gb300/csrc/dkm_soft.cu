@@ -13,9 +13,10 @@
 //              L_s = sum_ij w^T_ij ||p_i - c^T_j||^2.
 //
 // Every (point, centroid) quantity is recomputed, never stored: row passes
-// (one thread per point, reducing over the cloud's centroids in shared
-// memory) and column passes (one thread per centroid, reducing over a split
-// of the cloud's points staged in shared memory).  The backward recomputes
+// (two points per thread, reducing over the cloud's centroids in shared
+// memory) and column passes (two centroids per thread, reducing over a
+// split of the cloud's points staged in shared memory), both in packed
+// f32x2 arithmetic, whose lanes round as the scalar operations do.  The backward recomputes
 // the weights of step t from the checkpointed centroids c^t.  Column sums
 // run in FP32 over chunks of 64 points and in FP64 across chunks; splits
 // are combined in a fixed order, so results are deterministic.
@@ -30,7 +31,7 @@ namespace dkm {
 namespace {
 
 constexpr int kRowThreads = 256;
-constexpr int kSplit = 2048;       // points per column-pass CTA
+constexpr int kSplit = 512;        // points per column-pass CTA (several CTAs per SM for latency hiding)
 constexpr int kColChunk = 256;     // points staged in shared memory per round
 constexpr int kSubChunk = 64;      // FP32 accumulation run before the FP64 add
 
@@ -72,8 +73,45 @@ __device__ __forceinline__ float4 load_c(const float* C, int64_t j, float w) {
   return make_float4(C[j * D + 0], C[j * D + 1], D == 3 ? C[j * D + 2] : 0.f, w);
 }
 
-// Row pass.  Shared memory: c^t (k), and for kRowStep c^{t+1} with .w = 1/N
-// (k) and the upstream gradient of c^{t+1} (k).
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
+// sqd for two points at once (packed f32x2: each lane rounds as the scalar
+// form does)
+template <int D>
+__device__ __forceinline__ float2 sqd2(float2 px, float2 py, float2 pz, float4 c, float2& dx,
+                                       float2& dy, float2& dz) {
+  dx = __fadd2_rn(px, dup2(-c.x));
+  dy = __fadd2_rn(py, dup2(-c.y));
+  dz = D == 3 ? __fadd2_rn(pz, dup2(-c.z)) : make_float2(0.f, 0.f);
+  float2 s = __fmul2_rn(dx, dx);
+  s = __ffma2_rn(dy, dy, s);
+  if (D == 3) s = __ffma2_rn(dz, dz, s);
+  return s;
+}
+
+// softmax weights exp((m - s) / tau) / Z of two points
+__device__ __forceinline__ float2 weight2(float2 m, float2 s, float it, float2 iz) {
+  const float2 a = __fmul2_rn(__fadd2_rn(m, make_float2(-s.x, -s.y)), dup2(it));
+  return __fmul2_rn(make_float2(__expf(a.x), __expf(a.y)), iz);
+}
+
+// one point's step of the online normaliser: z = sum_j exp((m - D_ij) / tau)
+// against the running minimum m, rescaled by exp((m_new - m_old) / tau)
+// whenever the minimum drops.  The exponent is -|s - m| / tau either way.
+__device__ __forceinline__ void online_norm(float s, float& m, float& z, float it) {
+  const float e = __expf(-fabsf(__fadd_rn(s, -m)) * it);
+  const bool lower = s < m;
+  z = lower ? __fmaf_rn(z, e, 1.f) : __fadd_rn(z, e);
+  m = lower ? s : m;
+}
+
+// Row pass: each thread takes two points of its cloud, i and i + kRowThreads
+// of the CTA's 2 kRowThreads, evaluated together in packed f32x2 arithmetic
+// (each centroid read from shared memory once for both).  Shared memory:
+// c^t (k), and for kRowStep c^{t+1} with .w = 1/N (k) and the upstream
+// gradient of c^{t+1} (k).
+constexpr int kRowPoints = 2 * kRowThreads;   // points per row-pass CTA
+
 template <int D, int MODE>
 __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const float* __restrict__ Ct,
                                                           const float* __restrict__ Cn,
@@ -100,131 +138,168 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
     }
   }
   __syncthreads();
-  const int64_t i = o0 + (int64_t)blockIdx.x * kRowThreads + threadIdx.x;
-  const bool valid = i < o1;
-  const float3 p = valid ? load_pt<D>(A.P, i) : make_float3(0.f, 0.f, 0.f);
+  const int64_t i0 = o0 + (int64_t)blockIdx.x * kRowPoints + threadIdx.x;
+  const int64_t ii[2] = {i0, i0 + kRowThreads};
+  const bool vv[2] = {ii[0] < o1, ii[1] < o1};
+  const float3 pa = vv[0] ? load_pt<D>(A.P, ii[0]) : make_float3(0.f, 0.f, 0.f);
+  const float3 pb = vv[1] ? load_pt<D>(A.P, ii[1]) : make_float3(0.f, 0.f, 0.f);
   const float it = 1.f / A.tau[b];
   double contrib = 0.0;
-  float3 dv;
-  if (MODE == kRowHardBwd) {
-    // dOut/dp_i = dloss[b] * 2 (p_i - c_a(i)), a(i) the forward's label
-    if (valid) {
-      const int a = labels[i];
-      if (a < 0 || a >= k) {
-        atomicOr(A.bad, 1);
-        gP[i * D + 0] = gP[i * D + 1] = 0.f;
-        if (D == 3) gP[i * D + 2] = 0.f;
+  if (MODE == kRowHardBwd || MODE == kRowHard) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = ii[h];
+      const bool valid = vv[h];
+      const float3 p = h ? pb : pa;
+      float3 dv;
+      if (MODE == kRowHardBwd) {
+        // dOut/dp_i = dloss[b] * 2 (p_i - c_a(i)), a(i) the forward's label
+        if (valid) {
+          const int a = labels[i];
+          if (a < 0 || a >= k) {
+            atomicOr(A.bad, 1);
+            gP[i * D + 0] = gP[i * D + 1] = 0.f;
+            if (D == 3) gP[i * D + 2] = 0.f;
+          } else {
+            sqd<D>(p, sc[a], dv);
+            const float s2 = 2.f * (float)dloss[b];
+            gP[i * D + 0] = s2 * dv.x;
+            gP[i * D + 1] = s2 * dv.y;
+            if (D == 3) gP[i * D + 2] = s2 * dv.z;
+          }
+        }
       } else {
-        sqd<D>(p, sc[a], dv);
-        const float s2 = 2.f * (float)dloss[b];
-        gP[i * D + 0] = s2 * dv.x;
-        gP[i * D + 1] = s2 * dv.y;
-        if (D == 3) gP[i * D + 2] = s2 * dv.z;
-      }
-    }
-  } else if (MODE == kRowHard) {
-    float best = INFINITY;
-    int a = 0;
-    for (int j = 0; j < k; ++j) {
-      const float s = sqd<D>(p, sc[j], dv);
-      if (s < best) {
-        best = s;
-        a = j;
-      }
-    }
-    if (valid) {
-      labels[i] = a;
-      contrib = best;
-      if (gP) {
-        sqd<D>(p, sc[a], dv);
-        gP[i * D + 0] = 2.f * dv.x;
-        gP[i * D + 1] = 2.f * dv.y;
-        if (D == 3) gP[i * D + 2] = 2.f * dv.z;
+        float best = INFINITY;
+        int a = 0;
+        for (int j = 0; j < k; ++j) {
+          const float s = sqd<D>(p, sc[j], dv);
+          if (s < best) {
+            best = s;
+            a = j;
+          }
+        }
+        if (valid) {
+          labels[i] = a;
+          contrib += best;
+          if (gP) {
+            sqd<D>(p, sc[a], dv);
+            gP[i * D + 0] = 2.f * dv.x;
+            gP[i * D + 1] = 2.f * dv.y;
+            if (D == 3) gP[i * D + 2] = 2.f * dv.z;
+          }
+        }
       }
     }
   } else {
+    const float2 px = make_float2(pa.x, pb.x), py = make_float2(pa.y, pb.y),
+                 pz = make_float2(pa.z, pb.z);
+    float2 dx, dy, dz;
     const bool given = MODE == kRowStep && A.use_stats;
-    float m = INFINITY, iz = 0.f;
+    float2 m = dup2(INFINITY), iz = dup2(0.f);
     if (given) {   // the forward's statistics of this step (same values, bit for bit)
-      if (valid) {
-        m = A.m[i];
-        iz = A.iz[i];
+      if (vv[0]) {
+        m.x = A.m[ii[0]];
+        iz.x = A.iz[ii[0]];
+      }
+      if (vv[1]) {
+        m.y = A.m[ii[1]];
+        iz.y = A.iz[ii[1]];
       }
     } else {
-      // one sweep (online softmax normaliser, Milakov & Gimelshein 2018):
-      // z = sum_j exp((m - D_ij) / tau) for the running minimum m, rescaled
-      // by exp((m_new - m_old) / tau) <= 1 whenever the minimum drops
-      float z = 0.f;
+      // one sweep (online softmax normaliser, Milakov & Gimelshein 2018)
+      float2 z = dup2(0.f);
       for (int j = 0; j < k; ++j) {
-        const float sj = sqd<D>(p, sc[j], dv);
-        if (sj < m) {
-          z = __fmaf_rn(z, __expf((sj - m) * it), 1.f);
-          m = sj;
-        } else {
-          z += __expf((m - sj) * it);
-        }
+        const float2 s = sqd2<D>(px, py, pz, sc[j], dx, dy, dz);
+        online_norm(s.x, m.x, z.x, it);
+        online_norm(s.y, m.y, z.y, it);
       }
-      iz = 1.f / z;
+      iz = make_float2(1.f / z.x, 1.f / z.y);
     }
     if (MODE == kRowLoss || MODE == kRowLossBwd) {
       // E = sum_j w D;  B = sum_j w (p - c);  F = sum_j w D (p - c)
-      float E = 0.f;
-      float3 Bv = make_float3(0.f, 0.f, 0.f), F = make_float3(0.f, 0.f, 0.f);
+      float2 E = dup2(0.f);
+      float2 Bx = E, By = E, Bz = E, Fx = E, Fy = E, Fz = E;
       for (int j = 0; j < k; ++j) {
-        const float s = sqd<D>(p, sc[j], dv);
-        const float w = __expf((m - s) * it) * iz;
-        E = __fmaf_rn(w, s, E);
+        const float2 s = sqd2<D>(px, py, pz, sc[j], dx, dy, dz);
+        const float2 w = weight2(m, s, it, iz);
+        E = __ffma2_rn(w, s, E);
         if (MODE == kRowLossBwd) {
-          Bv.x = __fmaf_rn(w, dv.x, Bv.x); Bv.y = __fmaf_rn(w, dv.y, Bv.y); Bv.z = __fmaf_rn(w, dv.z, Bv.z);
-          const float ws = w * s;
-          F.x = __fmaf_rn(ws, dv.x, F.x); F.y = __fmaf_rn(ws, dv.y, F.y); F.z = __fmaf_rn(ws, dv.z, F.z);
+          Bx = __ffma2_rn(w, dx, Bx);
+          By = __ffma2_rn(w, dy, By);
+          Bz = __ffma2_rn(w, dz, Bz);
+          const float2 ws = __fmul2_rn(w, s);
+          Fx = __ffma2_rn(ws, dx, Fx);
+          Fy = __ffma2_rn(ws, dy, Fy);
+          Fz = __ffma2_rn(ws, dz, Fz);
         }
       }
-      if (valid) {
-        contrib = E;
+      const float sc2 = MODE == kRowLossBwd ? 2.f * (float)dloss[b] : 0.f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!vv[h]) continue;
+        const int64_t i = ii[h];
+        const float e = h ? E.y : E.x;
+        contrib += e;
         if (MODE == kRowLossBwd) {
           // dL/dp_i = 2 sum_l w_il (1 - (D_il - E_i)/tau) (p_i - c_l)
-          const float sc2 = 2.f * (float)dloss[b];
-          gP[i * D + 0] = sc2 * (Bv.x - it * (F.x - E * Bv.x));
-          gP[i * D + 1] = sc2 * (Bv.y - it * (F.y - E * Bv.y));
-          if (D == 3) gP[i * D + 2] = sc2 * (Bv.z - it * (F.z - E * Bv.z));
-          A.aux[i] = E;
+          const float bx = h ? Bx.y : Bx.x, by = h ? By.y : By.x, bz = h ? Bz.y : Bz.x;
+          const float fx = h ? Fx.y : Fx.x, fy = h ? Fy.y : Fy.x, fz = h ? Fz.y : Fz.x;
+          gP[i * D + 0] = sc2 * (bx - it * (fx - e * bx));
+          gP[i * D + 1] = sc2 * (by - it * (fy - e * by));
+          if (D == 3) gP[i * D + 2] = sc2 * (bz - it * (fz - e * bz));
+          A.aux[i] = e;
         }
       }
     } else if (MODE == kRowStep) {
       // rho = sum_j w g;  Av = sum_j w g (p - c^t);  Bv = sum_j w (p - c^t);
       // Dir = sum_j w gbar_j / N_j,  g_ij = gbar_j . (p_i - c^{t+1}_j) / N_j
-      float rho = 0.f;
-      float3 Av = make_float3(0.f, 0.f, 0.f), Bv = Av, Dir = Av;
+      float2 rho = dup2(0.f);
+      float2 Ax = rho, Ay = rho, Az = rho, Bx = rho, By = rho, Bz = rho, Dx = rho, Dy = rho,
+             Dz = rho;
       for (int j = 0; j < k; ++j) {
-        const float s = sqd<D>(p, sc[j], dv);
-        const float w = __expf((m - s) * it) * iz;
+        const float2 s = sqd2<D>(px, py, pz, sc[j], dx, dy, dz);
+        const float2 w = weight2(m, s, it, iz);
         const float4 cn = scn[j], gb = sg[j];
-        float3 dn;
-        sqd<D>(p, cn, dn);
-        float g = __fmul_rn(gb.x, dn.x);
-        g = __fmaf_rn(gb.y, dn.y, g);
-        if (D == 3) g = __fmaf_rn(gb.z, dn.z, g);
-        g *= cn.w;
-        const float wg = w * g;
-        rho += wg;
-        Av.x = __fmaf_rn(wg, dv.x, Av.x); Av.y = __fmaf_rn(wg, dv.y, Av.y); Av.z = __fmaf_rn(wg, dv.z, Av.z);
-        Bv.x = __fmaf_rn(w, dv.x, Bv.x); Bv.y = __fmaf_rn(w, dv.y, Bv.y); Bv.z = __fmaf_rn(w, dv.z, Bv.z);
-        const float wn = w * cn.w;
-        Dir.x = __fmaf_rn(wn, gb.x, Dir.x); Dir.y = __fmaf_rn(wn, gb.y, Dir.y); Dir.z = __fmaf_rn(wn, gb.z, Dir.z);
+        float2 nx, ny, nz;
+        sqd2<D>(px, py, pz, cn, nx, ny, nz);
+        float2 g = __fmul2_rn(dup2(gb.x), nx);
+        g = __ffma2_rn(dup2(gb.y), ny, g);
+        if (D == 3) g = __ffma2_rn(dup2(gb.z), nz, g);
+        g = __fmul2_rn(g, dup2(cn.w));
+        const float2 wg = __fmul2_rn(w, g);
+        rho = __fadd2_rn(rho, wg);
+        Ax = __ffma2_rn(wg, dx, Ax);
+        Ay = __ffma2_rn(wg, dy, Ay);
+        Az = __ffma2_rn(wg, dz, Az);
+        Bx = __ffma2_rn(w, dx, Bx);
+        By = __ffma2_rn(w, dy, By);
+        Bz = __ffma2_rn(w, dz, Bz);
+        const float2 wn = __fmul2_rn(w, dup2(cn.w));
+        Dx = __ffma2_rn(wn, dup2(gb.x), Dx);
+        Dy = __ffma2_rn(wn, dup2(gb.y), Dy);
+        Dz = __ffma2_rn(wn, dup2(gb.z), Dz);
       }
-      if (valid) {
-        // dL/dp_i += Dir + sum_j dD_ij 2 (p_i - c_j),  dD_ij = -(1/tau) w (g - rho)
-        const float two_it = 2.f * it;
-        gP[i * D + 0] += Dir.x - two_it * (Av.x - rho * Bv.x);
-        gP[i * D + 1] += Dir.y - two_it * (Av.y - rho * Bv.y);
-        if (D == 3) gP[i * D + 2] += Dir.z - two_it * (Av.z - rho * Bv.z);
-        A.aux[i] = rho;
+      // dL/dp_i += Dir + sum_j dD_ij 2 (p_i - c_j),  dD_ij = -(1/tau) w (g - rho)
+      const float two_it = 2.f * it;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!vv[h]) continue;
+        const int64_t i = ii[h];
+        const float r = h ? rho.y : rho.x;
+        gP[i * D + 0] += (h ? Dx.y : Dx.x) - two_it * ((h ? Ax.y : Ax.x) - r * (h ? Bx.y : Bx.x));
+        gP[i * D + 1] += (h ? Dy.y : Dy.x) - two_it * ((h ? Ay.y : Ay.x) - r * (h ? By.y : By.x));
+        if (D == 3)
+          gP[i * D + 2] += (h ? Dz.y : Dz.x) - two_it * ((h ? Az.y : Az.x) - r * (h ? Bz.y : Bz.x));
+        A.aux[i] = r;
       }
     }
-    if (valid && !given) {
-      A.m[i] = m;
-      A.iz[i] = iz;
+    if (!given) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!vv[h]) continue;
+        A.m[ii[h]] = h ? m.y : m.x;
+        A.iz[ii[h]] = h ? iz.y : iz.x;
+      }
     }
   }
   if (MODE == kRowLoss || MODE == kRowHard) {
@@ -241,31 +316,45 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
   }
 }
 
-// Column pass: one thread per centroid j of cloud blockIdx.y, over the
-// points of split blockIdx.x.  Writes part[b][s][j][0..3].
+// Column pass: each thread takes two centroids of cloud blockIdx.y, j and
+// j + blockDim.x, over the points of split blockIdx.x, evaluated together in
+// packed f32x2 arithmetic (each staged point read once for both).  Writes
+// part[b][s][j][0..3].
 template <int D, int MODE>
 __global__ void k_soft_col(SoftArgs A, const float* __restrict__ Ct, const float* __restrict__ Cn,
                            const float* __restrict__ Nn, const float* __restrict__ Gn,
                            const double* __restrict__ dloss, const int32_t* __restrict__ labels) {
   __shared__ float4 s_p[kColChunk];   // x, y, z, m
   __shared__ float4 s_q[kColChunk];   // iz, aux, label bits, -
-  const int b = blockIdx.y, s = blockIdx.x, k = A.k, j = threadIdx.x;
+  const int b = blockIdx.y, s = blockIdx.x, k = A.k;
+  const int jj[2] = {(int)threadIdx.x, (int)(threadIdx.x + blockDim.x)};
   const int64_t o0 = A.off[b], o1 = A.off[b + 1];
   const int64_t lo = o0 + (int64_t)s * kSplit, hi = min(lo + kSplit, o1);
-  const bool live = j < k;
-  const int64_t g = (int64_t)b * k + (live ? j : 0);
-  const float4 c = load_c<D>(Ct, g, 0.f);
-  float4 cn = c, gb = c;
-  float in = 0.f;
-  if (MODE == kColStep) {
-    cn = load_c<D>(Cn, g, 0.f);
-    gb = load_c<D>(Gn, g, 0.f);
-    const float n = Nn[g];
-    in = n > 0.f ? 1.f / n : 0.f;
+  const bool live[2] = {jj[0] < k, jj[1] < k};
+  float4 c[2], cn[2], gb[2];
+  float in[2] = {0.f, 0.f};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t g = (int64_t)b * k + (live[h] ? jj[h] : 0);
+    c[h] = load_c<D>(Ct, g, 0.f);
+    cn[h] = c[h];
+    gb[h] = c[h];
+    if (MODE == kColStep) {
+      cn[h] = load_c<D>(Cn, g, 0.f);
+      gb[h] = load_c<D>(Gn, g, 0.f);
+      const float n = Nn[g];
+      in[h] = n > 0.f ? 1.f / n : 0.f;
+    }
   }
+  const float2 ncx = make_float2(-c[0].x, -c[1].x), ncy = make_float2(-c[0].y, -c[1].y),
+               ncz = make_float2(-c[0].z, -c[1].z);
+  const float2 nnx = make_float2(-cn[0].x, -cn[1].x), nny = make_float2(-cn[0].y, -cn[1].y),
+               nnz = make_float2(-cn[0].z, -cn[1].z);
+  const float2 gbx = make_float2(gb[0].x, gb[1].x), gby = make_float2(gb[0].y, gb[1].y),
+               gbz = make_float2(gb[0].z, gb[1].z), in2 = make_float2(in[0], in[1]);
   const float it = 1.f / A.tau[b];
   const float scl = MODE == kColLoss ? (float)dloss[b] : 1.f;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
   for (int64_t c0 = lo; c0 < hi; c0 += kColChunk) {
     const int m = (int)min((int64_t)kColChunk, hi - c0);
     __syncthreads();
@@ -280,56 +369,73 @@ __global__ void k_soft_col(SoftArgs A, const float* __restrict__ Ct, const float
       }
     }
     __syncthreads();
-    if (!live) continue;
+    if (!live[0]) continue;   // (then j + blockDim.x is out of range too)
     for (int q0 = 0; q0 < m; q0 += kSubChunk) {
-      float f[4] = {0.f, 0.f, 0.f, 0.f};
+      float2 f0 = dup2(0.f), f1 = f0, f2 = f0, f3 = f0;   // .x: centroid j, .y: j + blockDim
       const int qe = min(q0 + kSubChunk, m);
       for (int q = q0; q < qe; ++q) {
         const float4 pq = s_p[q], aq = s_q[q];
-        const float3 p = make_float3(pq.x, pq.y, pq.z);
-        float3 dv;
         if (MODE == kColHard) {
           const int lq = __float_as_int(aq.z);
-          if (j == 0 && (lq < 0 || lq >= k)) atomicOr(A.bad, 1);
-          if (lq == j) {
-            sqd<D>(p, c, dv);
-            f[0] += dv.x; f[1] += dv.y; f[2] += dv.z;
+          if (threadIdx.x == 0 && (lq < 0 || lq >= k)) atomicOr(A.bad, 1);
+          if (lq == jj[0] || lq == jj[1]) {
+            const int h = lq == jj[1];
+            float3 dv;
+            sqd<D>(make_float3(pq.x, pq.y, pq.z), c[h], dv);
+            if (h) {
+              f0.y += dv.x; f1.y += dv.y; f2.y += dv.z;
+            } else {
+              f0.x += dv.x; f1.x += dv.y; f2.x += dv.z;
+            }
           }
           continue;
         }
-        const float sd = sqd<D>(p, c, dv);
-        const float w = __expf((pq.w - sd) * it) * aq.x;
+        const float2 dx = __fadd2_rn(dup2(pq.x), ncx), dy = __fadd2_rn(dup2(pq.y), ncy);
+        const float2 dz = D == 3 ? __fadd2_rn(dup2(pq.z), ncz) : dup2(0.f);
+        float2 sd = __fmul2_rn(dx, dx);
+        sd = __ffma2_rn(dy, dy, sd);
+        if (D == 3) sd = __ffma2_rn(dz, dz, sd);
+        const float2 a = __fmul2_rn(__fadd2_rn(dup2(pq.w), make_float2(-sd.x, -sd.y)), dup2(it));
+        const float2 w = __fmul2_rn(make_float2(__expf(a.x), __expf(a.y)), dup2(aq.x));
         if (MODE == kColMean) {
-          f[0] = __fmaf_rn(w, p.x, f[0]);
-          f[1] = __fmaf_rn(w, p.y, f[1]);
-          f[2] = __fmaf_rn(w, p.z, f[2]);
-          f[3] += w;
+          f0 = __ffma2_rn(w, dup2(pq.x), f0);
+          f1 = __ffma2_rn(w, dup2(pq.y), f1);
+          f2 = __ffma2_rn(w, dup2(pq.z), f2);
+          f3 = __fadd2_rn(f3, w);
         } else if (MODE == kColStep) {
-          float3 dn;
-          sqd<D>(p, cn, dn);
-          float gg = __fmul_rn(gb.x, dn.x);
-          gg = __fmaf_rn(gb.y, dn.y, gg);
-          if (D == 3) gg = __fmaf_rn(gb.z, dn.z, gg);
-          const float dd = -it * w * (gg * in - aq.y);   // dL/dD_ij
-          f[0] = __fmaf_rn(dd, dv.x, f[0]);
-          f[1] = __fmaf_rn(dd, dv.y, f[1]);
-          f[2] = __fmaf_rn(dd, dv.z, f[2]);
+          const float2 ex = __fadd2_rn(dup2(pq.x), nnx), ey = __fadd2_rn(dup2(pq.y), nny);
+          const float2 ez = D == 3 ? __fadd2_rn(dup2(pq.z), nnz) : dup2(0.f);
+          float2 gg = __fmul2_rn(gbx, ex);
+          gg = __ffma2_rn(gby, ey, gg);
+          if (D == 3) gg = __ffma2_rn(gbz, ez, gg);
+          // dL/dD_ij = -(1/tau) w (g_ij - rho_i)
+          const float2 dd = __fmul2_rn(__fmul2_rn(dup2(-it), w),
+                                       __ffma2_rn(gg, in2, dup2(-aq.y)));
+          f0 = __ffma2_rn(dd, dx, f0);
+          f1 = __ffma2_rn(dd, dy, f1);
+          f2 = __ffma2_rn(dd, dz, f2);
         } else {   // kColLoss: dL/dD_ij = w (1 - (D_ij - E_i) / tau)
-          const float dd = scl * w * (1.f - (sd - aq.y) * it);
-          f[0] = __fmaf_rn(dd, dv.x, f[0]);
-          f[1] = __fmaf_rn(dd, dv.y, f[1]);
-          f[2] = __fmaf_rn(dd, dv.z, f[2]);
+          const float2 u = __ffma2_rn(__fadd2_rn(sd, dup2(-aq.y)), dup2(-it), dup2(1.f));
+          const float2 dd = __fmul2_rn(__fmul2_rn(dup2(scl), w), u);
+          f0 = __ffma2_rn(dd, dx, f0);
+          f1 = __ffma2_rn(dd, dy, f1);
+          f2 = __ffma2_rn(dd, dz, f2);
         }
       }
-      for (int a = 0; a < 4; ++a) acc[a] += (double)f[a];
+      acc[0][0] += (double)f0.x; acc[0][1] += (double)f1.x;
+      acc[0][2] += (double)f2.x; acc[0][3] += (double)f3.x;
+      acc[1][0] += (double)f0.y; acc[1][1] += (double)f1.y;
+      acc[1][2] += (double)f2.y; acc[1][3] += (double)f3.y;
     }
   }
-  if (live) {
-    double* out = A.part + (((int64_t)b * A.ns + s) * k + j) * 4;
-    out[0] = acc[0];
-    out[1] = acc[1];
-    out[2] = acc[2];
-    out[3] = acc[3];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!live[h]) continue;
+    double* out = A.part + (((int64_t)b * A.ns + s) * k + jj[h]) * 4;
+    out[0] = acc[h][0];
+    out[1] = acc[h][1];
+    out[2] = acc[h][2];
+    out[3] = acc[h][3];
   }
 }
 
@@ -418,7 +524,7 @@ dkm_status soft_plan(const int64_t* offsets, int B, int d, int k, SoftPlan* P) {
     P->max_n = std::max(P->max_n, nb);
   }
   P->n_total = P->off[B];
-  P->gx = (int)((P->max_n + kRowThreads - 1) / kRowThreads);
+  P->gx = (int)((P->max_n + kRowPoints - 1) / kRowPoints);
   P->ns = (int)((P->max_n + kSplit - 1) / kSplit);
   return DKM_OK;
 }
@@ -495,7 +601,8 @@ template <int D, int MODE>
 void launch_col(const SoftArgs& A, const SoftPlan& P, const float* Ct, const float* Cn,
                 const float* Nn, const float* Gn, const double* dloss, const int32_t* lab,
                 cudaStream_t st) {
-  const int thr = std::max(32, (A.k + 31) / 32 * 32);
+  const int half = (A.k + 1) / 2;   // two centroids per thread
+  const int thr = std::max(32, (half + 31) / 32 * 32);
   k_soft_col<D, MODE><<<dim3(P.ns, A.B), thr, 0, st>>>(A, Ct, Cn, Nn, Gn, dloss, lab);
 }
 
