@@ -7,7 +7,7 @@ import pytest
 
 import oracle.soft_kmeans as sk
 from paper_2412_02244_gb300 import synth
-from gpu_util import torch_cuda
+from gpu_util import check_labels, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -264,3 +264,44 @@ def test_hard_sse_backward_scales_and_checks_labels(dkm):
     with pytest.raises(dkm.DkmError) as e:
         dkm.dkm_hard_sse_backward(Pt, off, B, d, k, Ct, bad, dl, gp, gc)
     assert e.value.status == dkm.DKM_EINVAL
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_soft_and_hard_with_odd_k_above_one_warp(dkm, oracle, d):
+    """k = 101: the column passes give each thread two centroids (j and j +
+    64 here), so both packed lanes are live for some threads and only the
+    first for others; clouds of 777 and 1,537 points end inside a row-pass
+    CTA (512 points) and a column split (512 points).  Soft forward and
+    backward and the hard SSE with both gradients against the oracle."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(71 + d)
+    clouds = [synth.gaussian_mixture_3d(n, 7, rng)[:, :d] for n in (777, 1537)]
+    k = 101
+    pts, P, init, off, tau = _batch(clouds, k, 72)
+    T = 2
+    dl = np.array([1.5, -0.75])
+    loss, ck, gp, gi = _gpu_soft(dkm, P, init, off, tau, T, dl)
+    for b, Pb in enumerate(pts):
+        P64, C64 = Pb.astype(np.float64), init[b].astype(np.float64)
+        L, Cs = sk.soft_forward(P64, C64, float(tau[b]), T)
+        ext = float(np.max(Pb.max(0) - Pb.min(0)))
+        assert abs(loss[b] - L) <= 1e-5 * L
+        for t in range(T + 1):
+            assert np.abs(ck[t, b] - Cs[t]).max() <= 1e-5 * ext
+        _, gP, gC = sk.soft_backward(P64, C64, float(tau[b]), T)
+        assert _rel(gp[off[b]:off[b + 1]], dl[b] * gP) <= GRAD_RTOL
+        assert _rel(gi[b], dl[b] * gC) <= GRAD_RTOL
+    Pt = torch.from_numpy(P).cuda()
+    Ct = torch.from_numpy(init).cuda()
+    hl = torch.empty(2, dtype=torch.float64, device="cuda")
+    lab = torch.empty(P.shape[0], dtype=torch.int32, device="cuda")
+    hp = torch.empty_like(Pt)
+    hc = torch.empty_like(Ct)
+    dkm.dkm_hard_sse(Pt, off, 2, d, k, Ct, lab, hl, hp, hc)
+    for b, Pb in enumerate(pts):
+        L, a, gP, gC = sk.hard_sse_grad(Pb.astype(np.float64), init[b].astype(np.float64))
+        lo, best, second = oracle.assign(Pb, init[b].astype(np.float64))
+        check_labels(lab.cpu().numpy()[off[b]:off[b + 1]], lo, best, second)   # near-ties only
+        assert abs(float(hl[b]) - L) <= 1e-5 * L
+        assert _rel(hp[off[b]:off[b + 1]].cpu().numpy(), gP) <= GRAD_RTOL
+        assert _rel(hc[b].cpu().numpy(), gC) <= GRAD_RTOL
