@@ -146,6 +146,27 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
   const float it = 1.f / A.tau[b];
   double contrib = 0.0;
   if (MODE == kRowHardBwd || MODE == kRowHard) {
+    // kRowHard: both points' nearest centroids first, in packed arithmetic;
+    // centroids come in ascending index order, so a strictly smaller
+    // distance is the only way to win and ties keep the lowest index
+    float2 hard_best = dup2(INFINITY);
+    int2 hard_a = make_int2(0, 0);
+    if (MODE == kRowHard) {
+      const float2 px = make_float2(pa.x, pb.x), py = make_float2(pa.y, pb.y),
+                   pz = make_float2(pa.z, pb.z);
+      float2 dx, dy, dz;
+      for (int j = 0; j < k; ++j) {
+        const float2 s = sqd2<D>(px, py, pz, sc[j], dx, dy, dz);
+        if (s.x < hard_best.x) {
+          hard_best.x = s.x;
+          hard_a.x = j;
+        }
+        if (s.y < hard_best.y) {
+          hard_best.y = s.y;
+          hard_a.y = j;
+        }
+      }
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t i = ii[h];
@@ -169,18 +190,10 @@ __global__ void __launch_bounds__(kRowThreads) k_soft_row(SoftArgs A, const floa
           }
         }
       } else {
-        float best = INFINITY;
-        int a = 0;
-        for (int j = 0; j < k; ++j) {
-          const float s = sqd<D>(p, sc[j], dv);
-          if (s < best) {
-            best = s;
-            a = j;
-          }
-        }
         if (valid) {
+          const int a = h ? hard_a.y : hard_a.x;
           labels[i] = a;
-          contrib += best;
+          contrib += h ? hard_best.y : hard_best.x;
           if (gP) {
             sqd<D>(p, sc[a], dv);
             gP[i * D + 0] = 2.f * dv.x;
