@@ -905,10 +905,29 @@ def main(argv=None):
                          "tile_cut_div=1,row_filter_min=256")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched-cloud and differentiable side measurements")
+    ap.add_argument("--soft-only", action="store_true",
+                    help="time only the differentiable workload (soft k-means forward + "
+                         "backward and the hard SSE, --steps timed calls each) and print its "
+                         "JSON object")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.soft_only:
+        return run_soft_only(args)
     return run_ours(args)
+
+
+def run_soft_only(args):
+    import torch
+    from paper_2412_02244_gb300 import build as b
+    b.build()
+    from paper_2412_02244_gb300 import dkm
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    peaks_dev = dkm.dkm_device_peaks(stream.cuda_stream)
+    print(json.dumps(bench_soft(dkm, torch, dev, stream, max(1, args.steps), peaks_dev)),
+          flush=True)
+    return 0
 
 
 if __name__ == "__main__":
