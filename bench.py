@@ -323,7 +323,7 @@ def launches_per_step(iters: int) -> int:
     return setup + run
 
 
-DEFAULT_TUNING = dict(cells_per_centroid=1.0, tile_cut_div=8, row_filter_min=48, sort_max=0,
+DEFAULT_TUNING = dict(cells_per_centroid=1.0, tile_cut_div=2, row_filter_min=48, sort_max=0,
                       tile_group=1, stay_test=0)
 ABLATIONS = [
     ("stay_test 1 (bound layer: tile test)", {"stay_test": 1}),

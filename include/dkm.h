@@ -266,7 +266,7 @@ typedef struct {
      * (0, max(4, opts.cells_per_centroid)] */
     float cells_per_centroid;
     /* a cloud's tiles are cut at the finest Morton cubes that add at most
-     * its 256-point windows / tile_cut_div tiles; 1 .. 1024 (default 8) */
+     * its 256-point windows / tile_cut_div tiles; 1 .. 1024 (default 2) */
     int tile_cut_div;
     /* tile candidate lists longer than this are filtered again per row of
      * 64 points (default 48; >= 256 turns the row filter off) */

@@ -82,7 +82,7 @@ struct dkm_ctx {
   int tiles_cap = 0;           // capacity of the tile arrays
   int n_tiles = 0;             // tiles of the current point index
   int tile_level = 0;          // Morton level whose cube boundaries cut cloud 0's tiles
-  int cut_div = 8;             // cube cuts may add n_windows / cut_div tiles per cloud
+  int cut_div = 2;             // cube cuts may add n_windows / cut_div tiles per cloud
   int unit_g = 1;              // tiles per search unit
   int n_units = 0;             // search units of the current tiling
   float cpc = 1.0f;            // grid cells per centroid (before the budget cap)

@@ -20,11 +20,11 @@ every context receives the same FP32 centroids C_t.
     distances where all points are checked, else the FP64 SSE of the GPU
     labels).
   - Then C_{t+1} = the oracle's update, rounded to FP32.
-The index settings are the defaults, the autotuner's usual choice on these
-workloads (tile_cut_div 2, row filter off), the bound layer (the tile stay
-test, and the tile and point stay tests) and hierarchical tiles
-(tile_group 4).  The free-running runs of the two 2D
-workloads are replayed pass by pass and compared with oracle.fit."""
+The index settings are the defaults, coarser tiles (tile_cut_div 8), the
+autotuner's usual choice on these workloads (tile_cut_div 2, row filter
+off), the bound layer (the tile stay test, and the tile and point stay
+tests) and hierarchical tiles (tile_group 4).  The free-running runs of the
+two 2D workloads are replayed pass by pass and compared with oracle.fit."""
 import numpy as np
 import pytest
 
@@ -37,6 +37,7 @@ pytestmark = pytest.mark.gpu
 SAMPLE = 200_000
 SETTINGS = {
     "default": {},
+    "coarse": dict(tile_cut_div=8),
     "tuned": dict(tile_cut_div=2, row_filter_min=256),
     "stay": dict(tile_cut_div=2, row_filter_min=256, stay_test=1),
     "pstay": dict(tile_cut_div=2, row_filter_min=256, stay_test=2),
