@@ -208,6 +208,9 @@ DKM_API dkm_status dkm_run(dkm_ctx* ctx, const float* init_centroids, int max_it
 
 /*
  * One-shot k-means: dkm_create + dkm_run + dkm_destroy.  opts may be NULL.
+ * The run's kernels are launched directly on the stream (a context's
+ * dkm_run captures them into a CUDA graph that later runs relaunch); the
+ * results are the same bit for bit.
  */
 DKM_API dkm_status dkm_fit(const float* points, int64_t n, int d, int k, const float* init_centroids,
                    int max_iter, float* centroids_out, int32_t* labels_out,

@@ -503,16 +503,15 @@ bool profiled_pass(int t, int iters, int period) {
   return t % period == (period - 1) / 2;
 }
 
-dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
-  destroy_graph(c);
+// The kernels of a run (prep, then per pass search, assignment, update),
+// enqueued on the context's stream: captured into the run graph, or
+// launched directly by a one-shot fit.  Returns the first launch error in
+// *e (a status other than DKM_OK comes from clearing the run buffers).
+dkm_status enqueue_run(dkm_ctx* c, const IterArgs& A0, int iters, int early, int profile,
+                       bool capturing, cudaError_t* e_out) {
+  // inside a capture the profiling events become external event nodes
+  const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   const int brute = c->opts.algo == DKM_ALGO_BRUTE;
-  const IterArgs A0 = iter_args(c, early, early);
-  if (profile) {
-    c->ev.resize((size_t)4 * iters);
-    for (auto& e : c->ev) DKM_CK(cudaEventCreate(&e));
-  }
-  cudaGraph_t g = nullptr;
-  DKM_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   dkm_status st = DKM_OK;
   cudaError_t e = cudaSuccess;
   do {
@@ -528,17 +527,37 @@ dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
       // (an early-stopping run may end on any pass: it counts every pass)
       A.want_stats = (early || t + 1 == iters) ? 1 : 0;
       const bool pe = profile && profiled_pass(t, iters, profile);
-      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 0], c->stream, evf))) break;
       if (!brute && (e = launch_search(A, par, c->d, c->stream))) break;
-      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 1], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 1], c->stream, evf))) break;
       if ((e = launch_assign(A, c->d, brute, c->stream))) break;
-      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 2], c->stream, evf))) break;
       const int insert = !brute && t + 1 < iters;
       if ((e = launch_centroids(A, 1, t, c->d, nullptr, insert, par ^ 1, nullptr, c->stream))) break;
       if (A.stay && insert && (e = launch_cbound(A, par ^ 1, c->d, 1, c->stream))) break;
-      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, cudaEventRecordExternal))) break;
+      if (pe && (e = cudaEventRecordWithFlags(c->ev[4 * t + 3], c->stream, evf))) break;
     }
   } while (0);
+  *e_out = e;
+  return st;
+}
+
+// per-pass profiling events of a run (created once per graph or fit)
+dkm_status make_run_events(dkm_ctx* c, int iters, int profile) {
+  if (!profile) return DKM_OK;
+  c->ev.resize((size_t)4 * iters);
+  for (auto& e : c->ev) DKM_CK(cudaEventCreate(&e));
+  return DKM_OK;
+}
+
+dkm_status build_run_graph(dkm_ctx* c, int iters, int early, int profile) {
+  destroy_graph(c);
+  const IterArgs A0 = iter_args(c, early, early);
+  DKM_TRY(make_run_events(c, iters, profile));
+  cudaGraph_t g = nullptr;
+  DKM_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  const dkm_status st = enqueue_run(c, A0, iters, early, profile, true, &e);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
   if (st != DKM_OK) {
     if (g) cudaGraphDestroy(g);
@@ -974,10 +993,25 @@ dkm_status run_impl(dkm_ctx* c, const float* init, int max_iter, float* centroid
   DKM_TRY(ensure_hist(c, max_iter));
   const int early = c->opts.early_stop ? 1 : 0;
   const int profile = c->opts.profile > 0 ? profile_period(c) : 0;   // 0 or the period
-  if (!graph_current(c, max_iter, early, profile))
-    DKM_TRY(build_run_graph(c, max_iter, early, profile));
-  if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
-  DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
+  if (c->one_shot) {
+    // a fit that destroys its context afterwards: capturing and
+    // instantiating a graph for a single launch would cost more host time
+    // than it saves, so the same kernels are launched directly
+    destroy_graph(c);
+    DKM_TRY(make_run_events(c, max_iter, profile));
+    if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
+    cudaError_t e = cudaSuccess;
+    DKM_TRY(enqueue_run(c, iter_args(c, early, early), max_iter, early, profile, false, &e));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DKM_ECUDA, "run launch failed: %s", cudaGetErrorString(e));
+    }
+  } else {
+    if (!graph_current(c, max_iter, early, profile))
+      DKM_TRY(build_run_graph(c, max_iter, early, profile));
+    if (profile) DKM_CK(cudaEventRecord(c->ev_a, c->stream));
+    DKM_CK(cudaGraphLaunch(c->gexec, c->stream));
+  }
   if (profile) DKM_CK(cudaEventRecord(c->ev_b, c->stream));
   // final labels in caller order + SSE of those labels against the final centroids
   IterArgs A = iter_args(c, 0, 0);
@@ -1458,6 +1492,7 @@ dkm_status dkm_fit(const float* points, int64_t n, int d, int k, const float* in
                    double* sse_out, const dkm_options* opts) {
   dkm_ctx* c = nullptr;
   DKM_TRY(dkm_create(&c, points, n, d, k, opts));
+  c->one_shot = true;
   dkm_status s = dkm_run(c, init, max_iter, centroids_out, labels_out, iterations_out, sse_out);
   std::string keep = g_last_error;
   dkm_destroy(c);
@@ -1471,6 +1506,7 @@ dkm_status dkm_fit_batched(const float* points, const int64_t* offsets, int B, i
                            double* sse_out, const dkm_options* opts) {
   dkm_ctx* c = nullptr;
   DKM_TRY(dkm_create_batched(&c, points, offsets, B, d, ks, opts));
+  c->one_shot = true;
   dkm_status s =
       dkm_run_batched(c, init, max_iter, centroids_out, labels_out, iterations_out, sse_out);
   std::string keep = g_last_error;

@@ -152,6 +152,7 @@ struct dkm_ctx {
 
   // cached iteration graph
   cudaGraphExec_t gexec = nullptr;
+  bool one_shot = false;       // dkm_fit: launch the run directly, no graph
   int g_iters = -1, g_algo = -1, g_early = -1, g_profile = -1;
   dkm::IterArgs g_args{};             // the kernel arguments the graph captured
   std::vector<cudaEvent_t> ev;        // per-pass events of the cached graph

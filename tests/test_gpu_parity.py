@@ -240,6 +240,25 @@ def test_host_buffers_match_device_buffers(dkm):
     assert np.array_equal(lab_h, lab_d.cpu().numpy())
 
 
+@pytest.mark.parametrize("early_stop,profile", [(0, 0), (1, 0), (0, 1)])
+def test_one_shot_fit_equals_context_run(dkm, early_stop, profile):
+    """dkm_fit launches the run's kernels directly instead of capturing a
+    graph; its outputs equal a context's dkm_run (graph launch) bit for bit."""
+    torch = torch_cuda()
+    w = SMALL["geo2d-blobs"]()
+    n, d, k = w.n, w.d, w.k
+    o = dkm.dkm_default_options(early_stop=early_stop, profile=profile)
+    C_f = torch.empty(k * d, dtype=torch.float32, device="cuda")
+    lab_f = torch.empty(n, dtype=torch.int32, device="cuda")
+    it_f, sse_f = dkm.dkm_fit(dev(w.points), n, d, k, dev(w.init), 20, C_f, lab_f, o)
+    ctx = make_ctx(dkm, w.points, k, early_stop=early_stop, profile=profile)
+    C_r, lab_r, it_r, sse_r = gpu_run(dkm, ctx, w.init, 20)
+    ctx.close()
+    assert it_f == it_r and sse_f == sse_r
+    assert np.array_equal(C_f.cpu().numpy().reshape(k, d), C_r)
+    assert np.array_equal(lab_f.cpu().numpy(), lab_r)
+
+
 def test_setup_reuse_new_points(dkm, oracle):
     w1 = synth.lidar3d(seed=41, n=50_000, k=64, n_objects=20)
     w2 = synth.lidar3d(seed=42, n=50_000, k=64, n_objects=20)
