@@ -438,6 +438,7 @@ dkm_status one_pass(dkm_ctx* c, bool track_changes) {
   IterArgs A = iter_args(c, track_changes ? 1 : 0, 0);
   DKM_CK(launch_centroids(A, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream));
   if (A.stay) DKM_CK(launch_cbound(A, 0, c->d, 0, c->stream));
+  if (!brute) DKM_CK(launch_seed_refs(A, 0, c->d, c->stream));
   if (!brute) DKM_CK(launch_search(A, 0, c->d, c->stream));
   DKM_CK(launch_assign(A, c->d, brute, c->stream));
   DKM_CK(launch_collect(A, -1, c->stream));
@@ -518,6 +519,7 @@ dkm_status enqueue_run(dkm_ctx* c, const IterArgs& A0, int iters, int early, int
     if ((st = zero_run_buffers(c, early != 0)) != DKM_OK) break;
     if ((e = launch_centroids(A0, 0, -1, c->d, c->cstage, !brute, 0, nullptr, c->stream))) break;
     if (A0.stay && (e = launch_cbound(A0, 0, c->d, 0, c->stream))) break;
+    if (!brute && (e = launch_seed_refs(A0, 0, c->d, c->stream))) break;
     for (int t = 0; t < iters; ++t) {
       const int par = t & 1;
       // a run returns the SSE of its final labels (computed after the

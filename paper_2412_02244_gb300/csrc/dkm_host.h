@@ -43,6 +43,7 @@ cudaError_t launch_reset_run(const IterArgs& A, cudaStream_t s);
 cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const float* user_c,
                              int insert, int par, int32_t* counts_out, cudaStream_t s);
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s);
+cudaError_t launch_seed_refs(const IterArgs& A, int par, int d, cudaStream_t s);
 cudaError_t launch_assign(const IterArgs& A, int d, int brute, cudaStream_t s);
 cudaError_t launch_collect(const IterArgs& A, int t, cudaStream_t s);
 cudaError_t launch_accum_labels(const IterArgs& A, int d, const int32_t* ulab,

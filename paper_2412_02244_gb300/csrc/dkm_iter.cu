@@ -1557,6 +1557,73 @@ cudaError_t launch_centroids(const IterArgs& A, int mode, int t, int d, const fl
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// k_seed_refs: a starting reference for every search unit that has none (a
+// fresh context, or tiles re-cut since the last run): the centroid nearest
+// to the centre of the unit's box among the centroids of the grid cell
+// holding that centre or, if it is empty, of the first non-empty shell of
+// cells around it (up to kSeedRings shells).  The reference only sets the
+// search's starting bound U = maxd(box, reference), which any centroid of
+// the cloud bounds validly, so the search's result does not depend on it;
+// without it the first search scans rings of cells with a looser bound and
+// keeps longer lists.  Units that already have a reference return at once.
+// One thread per unit; grid of parity `par`.
+// ---------------------------------------------------------------------------
+constexpr int kSeedRings = 3;
+
+__global__ void __launch_bounds__(kBlockThreads) k_seed_refs(const __grid_constant__ IterArgs A,
+                                                             int par, int d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.n_units) return;
+  const int b = A.B > 1 ? A.ucloud[t] : 0;
+  const Cloud& cl = A.B > 1 ? A.clouds[b] : A.cl0;
+  const int ref = A.tref[t];
+  if (ref >= cl.c0 && ref < cl.c0 + cl.k) return;
+  if (A.B > 1 && A.crun[b].done) return;
+  const Grid G = cl.grid;
+  const float4 lo = A.ubox[2 * t], hi = A.ubox[2 * t + 1];
+  const float px = 0.5f * (lo.x + hi.x), py = 0.5f * (lo.y + hi.y),
+              pz = d == 3 ? 0.5f * (lo.z + hi.z) : 0.f;
+  const int cx = cell_coord(px, G.g0[0], G.inv_s, G.dims[0]);
+  const int cy = cell_coord(py, G.g0[1], G.inv_s, G.dims[1]);
+  const int cz = d == 3 ? cell_coord(pz, G.g0[2], G.inv_s, G.dims[2]) : 0;
+  const int* __restrict__ gcnt = A.gcnt[par] + cl.cell0;
+  const float4* __restrict__ gbkt = A.gbkt[par] + cl.cell0 * kBucketCap;
+  float best = INFINITY;
+  int best_id = -1;
+  for (int r = 0; r <= kSeedRings && best_id < 0; ++r) {
+    const int zr = d == 3 ? r : 0;
+    for (int z = cz - zr; z <= cz + zr; ++z) {
+      if (z < 0 || z >= G.dims[2]) continue;
+      for (int y = cy - r; y <= cy + r; ++y) {
+        if (y < 0 || y >= G.dims[1]) continue;
+        for (int x = cx - r; x <= cx + r; ++x) {
+          if (x < 0 || x >= G.dims[0]) continue;
+          // the shell of Chebyshev radius r only
+          if (max(max(abs(x - cx), abs(y - cy)), abs(z - cz)) != r) continue;
+          const long long cell = ((long long)z * G.dims[1] + y) * G.dims[0] + x;
+          const int cnt = min(gcnt[cell], kBucketCap);
+          for (int i = 0; i < cnt; ++i) {
+            const float4 c = gbkt[cell * kBucketCap + i];
+            const float dx = c.x - px, dy = c.y - py, dz = c.z - pz;
+            const float dd = dx * dx + dy * dy + (d == 3 ? dz * dz : 0.f);
+            if (dd < best) {
+              best = dd;
+              best_id = __float_as_int(c.w);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (best_id >= 0) A.tref[t] = best_id;   // else the search scans rings itself
+}
+
+cudaError_t launch_seed_refs(const IterArgs& A, int par, int d, cudaStream_t s) {
+  k_seed_refs<<<ceil_div(A.n_units, kBlockThreads), kBlockThreads, 0, s>>>(A, par, d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_search(const IterArgs& A, int par, int d, cudaStream_t s) {
   const int g = ceil_div(A.n_units, kSearchWarps);
   if (d == 3) {
