@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "f16686977ac78a1e", "bytes_per_launch": 129_643_008 + 23_229_184,
+NCU_TRAFFIC = {"sha": "597aed86e51f6198", "bytes_per_launch": 129_607_424 + 22_846_464,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
