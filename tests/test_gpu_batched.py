@@ -6,7 +6,8 @@ batch only shares launches.  So every check compares cloud b of the batch
 with the oracle run on cloud b alone: lock-step labels and updates, the
 graph-captured run against the per-pass composition, a free-running fit
 with per-cloud early stop, and the 512-cloud uneven workload at full size
-(labels on sampled points, updates and SSE on all points)."""
+(all 25 passes in lock-step: labels on sampled points every pass and on all
+points at the first and last pass, updates and SSE on all points)."""
 import numpy as np
 import pytest
 
@@ -197,6 +198,59 @@ def test_batched_uneven_workload_full_size(dkm, oracle):
     assert flips <= 2
     # the run's final centroids are the 25th update of the composition
     assert np.array_equal(C25, C_u)
+
+
+def test_batched_full_size_lockstep(dkm, oracle):
+    """The 512-cloud workload at full size (Σn = 14.3M, Σk = 142,788), all 25
+    passes in lock-step with the oracle, cloud by cloud (Eq. 1; Algorithm 1's
+    refine step): every pass the indexed labels equal the GPU brute force on
+    all points; the labels equal the oracle's except at near-ties on a seeded
+    sample of 256 points per cloud, and on all points at the first and the
+    last pass; the update from the pass's own sums equals the oracle's update
+    of the same labels within 1e-5 of each cloud's extent, with equal cluster
+    sizes; the pass SSE is within 1e-4 of the oracle's SSE of those labels.
+    Then C_{t+1} = the oracle's update, rounded to FP32."""
+    ws = synth.batched3d(seed=4)
+    P, off, ks, coff, init = _batch(ws)
+    B = len(ks)
+    ctx = _ctx(dkm, P, off, ks)
+    dkm.dkm_set_tuning(ctx, cells_per_centroid=2.0, tile_cut_div=1, row_filter_min=256)
+    ctx_b = _ctx(dkm, P, off, ks, algo=dkm.DKM_ALGO_BRUTE)
+    rng = np.random.default_rng(44)
+    idx = [np.sort(rng.choice(int(off[b + 1] - off[b]), size=256, replace=False)).astype(np.int64)
+           for b in range(B)]
+    ext = [extent(P[off[b]:off[b + 1]]) for b in range(B)]
+    C = init.copy()
+    flips = 0
+    passes = 25
+    for t in range(passes):
+        lab_g, sse_g, _ = gpu_assign(dkm, ctx, C)
+        lab_b, sse_b, _ = gpu_assign(dkm, ctx_b, C)
+        assert np.array_equal(lab_g, lab_b), f"pass {t}: indexed labels differ from brute force"
+        C_g, cnt_g = gpu_update(dkm, ctx, None, C)   # the pass's own sums
+        full = t == 0 or t == passes - 1
+        C_next = np.empty_like(C)
+        sse_o = 0.0
+        for b in range(B):
+            ps, cs = slice(off[b], off[b + 1]), slice(coff[b], coff[b + 1])
+            Pb, Cb = P[ps], C[cs].astype(np.float64)
+            if full:
+                lab_o, best, second = oracle.assign(Pb, Cb)
+                flips += check_labels(lab_g[ps], lab_o, best, second)
+            else:
+                lab_o, best, second = oracle.assign_subset(Pb, idx[b], Cb)
+                flips += check_labels(lab_g[ps][idx[b]], lab_o, best, second)
+            sse_o += oracle.sse(Pb, lab_g[ps], Cb)
+            C_o, cnt_o = oracle.update(Pb, lab_g[ps], Cb)
+            assert np.array_equal(cnt_g[cs], cnt_o), f"pass {t} cloud {b}: cluster sizes"
+            err = np.abs(C_g[cs].astype(np.float64) - C_o).max()
+            assert err <= CENTROID_TOL * ext[b], f"pass {t} cloud {b}: centroid error {err:.3g}"
+            C_next[cs] = C_o.astype(np.float32)
+        assert abs(sse_g - sse_o) <= SSE_RTOL * sse_o, f"pass {t}: SSE"
+        C = C_next
+    ctx.close()
+    ctx_b.close()
+    assert flips <= 50
 
 
 @pytest.mark.parametrize("setting", [dict(cells_per_centroid=0.5), dict(cells_per_centroid=4.0),
