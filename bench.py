@@ -905,6 +905,10 @@ def main(argv=None):
                          "tile_cut_div=1,row_filter_min=256")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched-cloud and differentiable side measurements")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the 512-cloud workload (autotuned, --steps timed steps of "
+                         "setup + 25 passes, and its brute-force comparison) and print its JSON "
+                         "object")
     ap.add_argument("--soft-only", action="store_true",
                     help="time only the differentiable workload (soft k-means forward + "
                          "backward and the hard SSE, --steps timed calls each) and print its "
@@ -914,7 +918,21 @@ def main(argv=None):
         return run_reference(args)
     if args.soft_only:
         return run_soft_only(args)
+    if args.batched_only:
+        return run_batched_only(args)
     return run_ours(args)
+
+
+def run_batched_only(args):
+    import torch
+    from paper_2412_02244_gb300 import build as b
+    b.build()
+    from paper_2412_02244_gb300 import dkm
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    hbm, _ = peaks()
+    print(json.dumps(bench_batched(dkm, torch, dev, stream, max(1, args.steps), hbm)), flush=True)
+    return 0
 
 
 def run_soft_only(args):
