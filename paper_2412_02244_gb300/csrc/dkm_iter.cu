@@ -1397,7 +1397,28 @@ __device__ __forceinline__ void assign_tile(const IterArgs& A, int t, float4* __
     const int s_t = residual_scale(warp_max_nonneg(m2));
     if (q_tile <= 32) {
       single = tile_sums_rows<D>(A, P, bid, va, vb, nv_row, s_t, q_tile, sc, sacc, s_glob);
+    } else if (MULTI) {
+      // Batches of dense clouds (where most long lists occur): each point's
+      // residual quantized once against its own staged centroid, then
+      // grouped by list position over the whole tile.  (The single-cloud
+      // kernel keeps the form below: these registers would spill on its
+      // hot path.)
+      const float scl = pow2f(s_t);
+      unsigned qx[kPts], qy[kPts], qz[kPts];
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r) {
+        const float4 ca = sc[gk[2 * r]], cb = sc[gk[2 * r + 1]];
+        qx[2 * r] = quantize(__fadd_rn(P.x[r].x, -ca.x), scl);
+        qy[2 * r] = quantize(__fadd_rn(P.y[r].x, -ca.y), scl);
+        qz[2 * r] = D == 3 ? quantize(__fadd_rn(P.z[r].x, -ca.z), scl) : kMagicBits;
+        qx[2 * r + 1] = quantize(__fadd_rn(P.x[r].y, -cb.x), scl);
+        qy[2 * r + 1] = quantize(__fadd_rn(P.y[r].y, -cb.y), scl);
+        qz[2 * r + 1] = D == 3 ? quantize(__fadd_rn(P.z[r].y, -cb.z), scl) : kMagicBits;
+      }
+      single = tile_sums<D>(A, qx, qy, qz, gk, pv, s_t, true, false, sc, s_glob);
     } else {
+      // each group re-quantizes its points on the fly (no per-point
+      // residuals kept in registers)
       unsigned gs[2] = {0u, 0u}, pm = 0u;
 #pragma unroll
       for (int h = 0; h < kPts; ++h) {
