@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 ASSIGN_BYTES_PER_POINT = 16
 # DRAM bytes (read + write) of one k_assign launch from the committed ncu
 # capture, valid only while the kernel source is unchanged
-NCU_TRAFFIC = {"sha": "597aed86e51f6198", "bytes_per_launch": 129_607_424 + 22_846_464,
+NCU_TRAFFIC = {"sha": "22bdb079b0baa2f4", "bytes_per_launch": 129_609_984 + 22_913_536,
                "source": "profiles/k_assign_lidar3d_n1e7_k1e4.md"}
 
 
